@@ -1,0 +1,158 @@
+"""Pins for the oracle's dipolar potential (convolution theorem with
+U(k) = (4 pi/3)(3 kz^2/k^2 - 1), U(0) = 0) and the quasi-2D XY kernel:
+exact single Fourier modes, a continuum closed form for a Gaussian density,
+a brute-force direct-space sum, and quadrature of the 3D kernel."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import oracle
+from paper_1601_04640_gb300 import synth
+
+
+def _grid(n, h):
+    x = [synth.axis(n[a], h[a]) for a in range(len(n))]
+    return np.meshgrid(*reversed(x), indexing="ij")  # Z, Y, X (3D) or Y, X
+
+
+def _p3(n, h):
+    return oracle.Params(dim=3, n=n, h=h, nu=(1, 1, 1), kernel="dipolar3d")
+
+
+@pytest.mark.parametrize("axis,m,factor", [
+    (2, 1, 8 * math.pi / 3),      # k along z: U = (4pi/3)(3 - 1)
+    (2, 3, 8 * math.pi / 3),
+    (0, 2, -4 * math.pi / 3),     # k along x: U = (4pi/3)(0 - 1)
+    (1, 5, -4 * math.pi / 3),
+])
+def test_single_mode(axis, m, factor):
+    n, h = (16, 12, 20), (0.3, 0.4, 0.25)
+    Z, Y, X = _grid(n, h)
+    c = (X, Y, Z)[axis]
+    k = 2 * math.pi * m / (n[axis] * h[axis])
+    eps = 0.1
+    dens = 1.0 + eps * np.cos(k * c)
+    phi = oracle.dipolar_potential(_p3(n, h), dens)
+    assert np.max(np.abs(phi - factor * eps * np.cos(k * c))) < 1e-12
+
+
+def test_diagonal_mode_and_constant():
+    n, h = (16, 16, 16), (0.25, 0.25, 0.25)
+    Z, Y, X = _grid(n, h)
+    k = 2 * math.pi * 2 / (n[0] * h[0])
+    dens = 2.0 + 0.3 * np.cos(k * X + k * Z)      # 3 cos^2 = 3/2
+    phi = oracle.dipolar_potential(_p3(n, h), dens)
+    assert np.max(np.abs(phi - 0.3 * (2 * math.pi / 3) * np.cos(k * X + k * Z))) < 1e-12
+    phi0 = oracle.dipolar_potential(_p3(n, h), np.full(Z.shape, 3.7))
+    assert np.max(np.abs(phi0)) < 1e-13
+
+
+def _gaussian_phi(X, Y, Z, sigma):
+    """Continuum Phi for n = (2 pi s^2)^(-3/2) exp(-r^2/(2 s^2)):
+    (1 - 3 cos^2)/r^3 = -d_z^2 (1/r) - (4 pi/3) delta, so
+    Phi = -d_z^2 phiN - (4 pi/3) n with phiN = erf(r/a)/r, a = sqrt(2) s."""
+    a = math.sqrt(2.0) * sigma
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    n = (2 * math.pi * sigma ** 2) ** -1.5 * np.exp(-r * r / (2 * sigma ** 2))
+    c0 = 2.0 / (a * math.sqrt(math.pi))
+    small = r < 0.05 * a
+    rs = np.where(small, 1.0, r)
+    E = special.erf(rs / a)
+    E1 = c0 * np.exp(-rs * rs / (a * a))
+    E2 = -(2 * rs / (a * a)) * E1
+    d1 = E1 / rs - E / rs ** 2                    # phiN'
+    d2 = E2 / rs - 2 * E1 / rs ** 2 + 2 * E / rs ** 3   # phiN''
+    d1_over_r = d1 / rs
+    # series phiN = c0 (1 - r^2/(3a^2) + r^4/(10 a^4)) near the origin
+    c2, c4 = -c0 / (3 * a * a), c0 / (10 * a ** 4)
+    d1_over_r = np.where(small, 2 * c2 + 4 * c4 * r * r, d1_over_r)
+    d2 = np.where(small, 2 * c2 + 12 * c4 * r * r, d2)
+    cz2 = np.where(r > 0, Z * Z / np.where(r > 0, r * r, 1.0), 1.0 / 3.0)
+    dzz = d2 * cz2 + d1_over_r * (1.0 - cz2)
+    return -dzz - (4 * math.pi / 3) * n, n
+
+
+def test_gaussian_closed_form():
+    """Anisotropic spacing (hz != hx) pins the k-grid scaling and the axis.
+    The remaining difference is the periodic-image field, which falls as
+    (sigma/L)^3: check the level and the cubic rate between two boxes."""
+    sigma = 0.6
+    errs = []
+    for L in (8.0, 12.0):
+        n = (int(L / 0.25), int(L / 0.25), int(L / 0.2))
+        h = (0.25, 0.25, 0.2)
+        Z, Y, X = _grid(n, h)
+        ref, dens = _gaussian_phi(X, Y, Z, sigma)
+        phi = oracle.dipolar_potential(_p3(n, h), dens)
+        errs.append(np.max(np.abs((phi - phi.mean()) - (ref - ref.mean()))) / np.max(np.abs(ref)))
+    assert errs[1] < 0.02
+    assert 2.8 < errs[0] / errs[1] < 4.0      # (12/8)^3 = 3.375
+
+
+def _brute(n, h, dens):
+    """Direct sum h^3 sum_{j != i} (1 - 3 cos^2 theta_ij)/r_ij^3 n_j over the
+    minimum-image box (the on-site cell integrates to zero by cubic symmetry)."""
+    Z, Y, X = _grid((n, n, n), (h, h, h))
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    nn = dens.ravel()
+    L = n * h
+    out = np.empty(len(pts))
+    for i in range(len(pts)):
+        d = pts - pts[i]
+        d -= L * np.round(d / L)
+        r2 = (d * d).sum(1)
+        r2[i] = 1.0
+        u = (1.0 - 3.0 * d[:, 2] ** 2 / r2) / r2 ** 1.5
+        u[i] = 0.0
+        out[i] = h ** 3 * np.dot(u, nn)
+    return out.reshape(dens.shape)
+
+
+def test_brute_force_direct_sum_converges():
+    """FFT route vs brute-force real-space sum on tiny grids: the discrepancy
+    comes from periodic images and falls as the box grows (h fixed)."""
+    errs = []
+    for n in (16, 24):
+        h = 0.5
+        Z, Y, X = _grid((n, n, n), (h, h, h))
+        dens = np.exp(-(X ** 2 + Y ** 2 + (Z / 1.3) ** 2) / (2 * 0.81))
+        f = oracle.dipolar_potential(_p3((n, n, n), (h, h, h)), dens)
+        b = _brute(n, h, dens)
+        f -= f.mean()
+        b -= b.mean()
+        errs.append(np.max(np.abs(f - b)) / np.max(np.abs(f)))
+    assert errs[1] < errs[0]
+    assert errs[1] < 0.06
+
+
+def test_cubic_symmetry_zero_energy():
+    """On a cubic grid a density symmetric under axis permutations has
+    sum n Phi = 0 (the angular average of 3 cos^2 - 1 vanishes)."""
+    n, h = (16, 16, 16), (0.4, 0.4, 0.4)
+    Z, Y, X = _grid(n, h)
+    dens = np.exp(-(X ** 2 + Y ** 2 + Z ** 2)) + 0.3 * np.exp(-((X * Y) ** 2 + (Y * Z) ** 2 + (X * Z) ** 2))
+    phi = oracle.dipolar_potential(_p3(n, h), dens)
+    assert abs(np.sum(phi * dens)) < 1e-12 * np.sum(np.abs(phi * dens))
+
+
+@pytest.mark.parametrize("k", [0.0, 0.3, 1.0, 2.5, 7.0, 20.0])
+@pytest.mark.parametrize("d", [0.5, 1.0])
+def test_quasi2d_kernel_vs_quadrature(k, d):
+    """U2(k) = int dkz/(2pi) (4pi/3)(3 kz^2/(k^2 + kz^2) - 1) exp(-kz^2 d^2/2)."""
+    f = lambda kz: (4 * math.pi / 3) * (3 * kz * kz / (k * k + kz * kz) - 1) * math.exp(-kz * kz * d * d / 2) / (2 * math.pi) if (k > 0 or kz != 0) else -(4 * math.pi / 3) / (2 * math.pi)
+    val, _ = integrate.quad(f, -np.inf, np.inf, epsabs=1e-13, epsrel=1e-12, limit=400)
+    assert abs(oracle.q2d_value(k, d) - val) < 1e-10 * max(1.0, abs(val))
+
+
+def test_quasi2d_single_mode():
+    n, h, d = (24, 20), (0.2, 0.3), 0.5
+    Y, X = _grid(n, h)
+    kx = 2 * math.pi * 3 / (n[0] * h[0])
+    p = oracle.Params(dim=2, n=n, h=h, nu=(1, 1), kernel="quasi2d", qd=d)
+    dens = 1.0 + 0.2 * np.cos(kx * X)
+    phi = oracle.dipolar_potential(p, dens)
+    U0 = oracle.q2d_value(0.0, d)
+    ref = U0 * 1.0 + 0.2 * oracle.q2d_value(kx, d) * np.cos(kx * X)
+    assert np.max(np.abs(phi - ref)) < 1e-12
