@@ -1,0 +1,162 @@
+/*
+ * dgpe.h -- C ABI of the GB300-native split-step Crank-Nicolson solver for the
+ * dipolar Gross-Pitaevskii equation (arXiv:1601.04640: "Nature of problem",
+ * "Solution method").
+ *
+ * Equation solved (dimensionless trap units, "Nature of problem"):
+ *   i dpsi/dt = [ -1/2 lap + V + g |psi|^2 + g_dd Phi_d ] psi
+ *   V = s(t) * 1/2 (nu_x^2 x^2 + nu_y^2 y^2 [+ nu_z^2 z^2]),
+ *   s(t) = 1 + sum_{m=1..M} c_m sin(m t)        (s = 1 unless set),
+ *   Phi_d = IDFT[ U(k) DFT(|psi|^2) ] / N,  U(k) = (4 pi/3)(3 kz^2/k^2 - 1),
+ *   U(0) = 0 (3D); quasi-2D XY: U(k) averaged over a Gaussian z-profile of
+ *   width d ("Solution method": Fourier transform + convolution theorem).
+ * One time step ("Solution method", the functions of "Summary of revisions"):
+ *   1. Phi_d from the step-start density (calcpsidd2);
+ *   2. psi <- exp(-kappa dt (V + g|psi|^2 + g_dd Phi_d)) psi, kappa = i in real
+ *      time, 1 in imaginary time (calcnu);
+ *   3. Crank-Nicolson along x, y (, z): (I + kappa tau T) psi+ =
+ *      (I - kappa tau T) psi on every grid line, tau = dt/(4 h^2),
+ *      T = tridiag(-1, 2, -1), Dirichlet ghosts psi_{-1} = psi_N = 0
+ *      (calclux, calcluy, calcluz);
+ *   4. imaginary time only: psi <- psi / sqrt(h^d sum |psi|^2) (calcnorm).
+ * Grid: x_i = (i - N/2) h; psi is row-major with x fastest: [z][y][x] (3D),
+ * [y][x] (2D XY).  Interleaved complex (re, im).
+ *
+ * Conventions of every call:
+ *   - return DGPE_OK (0) or a negative DGPE_E* code; nothing aborts or traps;
+ *     dgpe_last_error() gives the text of the last failure of a handle;
+ *   - the library owns every device buffer it allocates; the caller owns the
+ *     CUDA stream passed to dgpe_create (NULL = the legacy default stream) and
+ *     every host or device buffer it passes in;
+ *   - work is enqueued on the handle's stream; calls that return data to the
+ *     host (get_psi, observables, sync) synchronise that stream, and errors of
+ *     earlier asynchronous work surface there as DGPE_ECUDA.
+ */
+#ifndef DGPE_H
+#define DGPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DGPE_OK 0
+#define DGPE_EINVAL (-1)        /* bad argument or parameter */
+#define DGPE_EUNSUPPORTED (-2)  /* valid but not supported (grid size, XZ plane) */
+#define DGPE_ENOMEM (-3)        /* device allocation failed */
+#define DGPE_ECUDA (-4)         /* a CUDA call failed */
+#define DGPE_ENONFINITE (-5)    /* NaN or Inf found in the state */
+#define DGPE_ETIMEOUT (-6)      /* a bounded device-side wait ran out */
+
+/* dgpe_params.mode */
+#define DGPE_IMAG 0             /* imaginary time: stationary states */
+#define DGPE_REAL 1             /* real time: dynamics */
+/* dgpe_params.precision */
+#define DGPE_FP64 0             /* every substep in FP64 */
+#define DGPE_FP32_BULK 1        /* FFT, exponential and Thomas arithmetic and
+                                   the state in FP32; norm/mu/energy reductions,
+                                   renormalisation and all tables built in FP64 */
+/* dgpe_params.kernel */
+#define DGPE_KERNEL_NONE 0
+#define DGPE_KERNEL_DIPOLAR_3D 1
+#define DGPE_KERNEL_QUASI2D_XY 2
+/* dgpe_params.plane (2D only) */
+#define DGPE_PLANE_XY 0
+#define DGPE_PLANE_XZ 1         /* returns DGPE_EUNSUPPORTED */
+/* dgpe_params.flags */
+#define DGPE_FLAG_NO_GRAPH 1u   /* launch the passes directly instead of
+                                   replaying a captured CUDA graph */
+
+typedef struct dgpe_params {
+  int dim;          /* 2 or 3 */
+  int plane;        /* DGPE_PLANE_* (2D) */
+  int n[3];         /* nx, ny, nz (nz ignored in 2D); each a power of two
+                       between 32 and 512 (other 2^a 3^b 5^c lengths return
+                       DGPE_EUNSUPPORTED) */
+  double h[3];      /* spacings hx, hy, hz > 0 */
+  double nu[3];     /* trap frequencies nu_x, nu_y, nu_z >= 0 */
+  double g;         /* contact strength */
+  double gdd;       /* dipolar strength */
+  double dt;        /* time step > 0 */
+  int mode;         /* DGPE_IMAG or DGPE_REAL */
+  int precision;    /* DGPE_FP64 or DGPE_FP32_BULK */
+  int kernel;       /* DGPE_KERNEL_* (DIPOLAR_3D needs dim 3, QUASI2D_XY dim 2) */
+  double qd;        /* quasi-2D z-width d > 0 (QUASI2D_XY only) */
+  unsigned flags;   /* DGPE_FLAG_* */
+} dgpe_params;
+
+typedef struct dgpe_obs {
+  double norm;      /* h^d sum |psi|^2 */
+  double mu;        /* chemical potential, per particle (divided by norm) */
+  double energy;    /* energy per particle (divided by norm) */
+  double rms[3];    /* sqrt(<x^2>), sqrt(<y^2>), sqrt(<z^2>) (0 for z in 2D) */
+  double rms_r;     /* sqrt(<r^2>) */
+  double t;         /* time of the state: steps taken * dt */
+  double kin;       /* kinetic energy per particle: 1/2 sum_a sum |psi_{i+1} -
+                       psi_i|^2 / h_a^2 over forward differences, ghosts 0 */
+  double pot;       /* trap energy per particle */
+  double contact;   /* g sum |psi|^4 h^d / norm */
+  double dipolar;   /* g_dd sum Phi_d |psi|^2 h^d / norm */
+} dgpe_obs;
+
+typedef struct dgpe_solver *dgpe_t;
+
+/* Create a solver for one condensate.  Validates p, allocates psi (zero), the
+ * half spectrum and the tables, builds U(k)/N, the Thomas tables and the FFT
+ * roots in FP64, and captures one step into a CUDA graph.  cuda_stream is a
+ * cudaStream_t (or NULL).  On failure *out is NULL. */
+int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_t *out);
+
+/* Release every resource of h; NULL is a no-op. */
+void dgpe_destroy(dgpe_t h);
+
+/* Copy the state in/out as host FP64 interleaved complex, n_sites =
+ * nx*ny(*nz) complex values.  set_psi starts the time at t = 0 unless
+ * dgpe_set_time is called after it.  get_psi synchronises. */
+int dgpe_set_psi(dgpe_t h, const double *psi, size_t n_sites);
+int dgpe_get_psi(dgpe_t h, double *psi, size_t n_sites);
+
+/* Device-pointer variants: psi is a device buffer of n_sites complex values,
+ * complex128 when fp64 != 0, else complex64.  Asynchronous on the stream. */
+int dgpe_set_psi_device(dgpe_t h, const void *psi, size_t n_sites, int fp64);
+int dgpe_get_psi_device(dgpe_t h, void *psi, size_t n_sites, int fp64);
+
+/* Advance n >= 0 steps (graph replays).  Asynchronous. */
+int dgpe_step(dgpe_t h, int n);
+
+/* norm, mu, energy, rms sizes of the current state in FP64 (calcmuen,
+ * calcrms, calcnorm).  Synchronises.  DGPE_ENONFINITE if the state holds a
+ * NaN or an Inf. */
+int dgpe_observables(dgpe_t h, dgpe_obs *o);
+
+/* Phi_d of the current density, written to a host FP64 array of n_sites
+ * reals (calcpsidd2).  Synchronises. */
+int dgpe_dipolar_potential(dgpe_t h, double *phi, size_t n_sites);
+
+/* Change the contact strength (a quench), the mode (imaginary <-> real) or the
+ * trap modulation V(t) = V0 (1 + sum_{m=1..M} c_m sin(m t)), M <= 16. */
+int dgpe_set_g(dgpe_t h, double g);
+int dgpe_set_mode(dgpe_t h, int mode);
+int dgpe_set_trap_modulation(dgpe_t h, const double *c, int M);
+
+/* Step counter n of the next step (its time is t_n = n dt). */
+int dgpe_set_time(dgpe_t h, long long step);
+int dgpe_get_time(dgpe_t h, long long *step);
+
+/* Wait for all work of h; report asynchronous errors. */
+int dgpe_sync(dgpe_t h);
+
+/* Number of kernel launches one dgpe_step(1) makes. */
+int dgpe_launches_per_step(dgpe_t h);
+
+/* Text of the last error of h (or of the last failed dgpe_create when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char *dgpe_last_error(dgpe_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGPE_H */

@@ -1,0 +1,394 @@
+// dgpe_device.cuh -- device building blocks of the GB300 split-step solver:
+// complex arithmetic, small DFT codelets, a shared-memory Stockham FFT over a
+// tile of lines, the chunk-parallel Thomas solve of one Crank-Nicolson
+// substep, and deterministic FP64 block reductions.
+//
+// The method ("Solution method" of arXiv:1601.04640): the dipolar potential is
+// a convolution evaluated with FFTs; the kinetic substeps are Crank-Nicolson
+// tridiagonal solves along x, y, z ("Summary of revisions": calclux, calcluy,
+// calcluz).  Everything here is written for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgpe {
+
+// ------------------------------------------------------------ complex type
+template <typename R> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
+template <typename R> using cx = typename V2<R>::T;
+
+template <typename R> __device__ __forceinline__ cx<R> mk(R x, R y) {
+  cx<R> c; c.x = x; c.y = y; return c;
+}
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename C> __device__ __forceinline__ C cmulconj(C a, C b) {  // a * conj(b)
+  C c; c.x = a.x * b.x + a.y * b.y; c.y = a.y * b.x - a.x * b.y; return c;
+}
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
+  C c; c.x = a.x * s; c.y = a.y * s; return c;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __device__ __forceinline__ C czero() { C c; c.x = 0; c.y = 0; return c; }
+
+// Thomas coefficients are real in imaginary time and complex in real time.
+__device__ __forceinline__ double2 coef_mul(double s, double2 v) { return make_double2(s * v.x, s * v.y); }
+__device__ __forceinline__ float2 coef_mul(float s, float2 v) { return make_float2(s * v.x, s * v.y); }
+__device__ __forceinline__ double2 coef_mul(double2 s, double2 v) { return cmul(s, v); }
+__device__ __forceinline__ float2 coef_mul(float2 s, float2 v) { return cmul(s, v); }
+__device__ __forceinline__ double coef_prod(double a, double b) { return a * b; }
+__device__ __forceinline__ float coef_prod(float a, float b) { return a * b; }
+__device__ __forceinline__ double2 coef_prod(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float2 coef_prod(float2 a, float2 b) { return cmul(a, b); }
+template <typename T> __device__ __forceinline__ T coef_zero();
+template <> __device__ __forceinline__ double coef_zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float coef_zero<float>() { return 0.0f; }
+template <> __device__ __forceinline__ double2 coef_zero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 coef_zero<float2>() { return make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ double coef_scale(double c, double s) { return c * s; }
+__device__ __forceinline__ float coef_scale(float c, float s) { return c * s; }
+__device__ __forceinline__ double2 coef_scale(double2 c, double s) { return make_double2(c.x * s, c.y * s); }
+__device__ __forceinline__ float2 coef_scale(float2 c, float s) { return make_float2(c.x * s, c.y * s); }
+template <typename T> __device__ __forceinline__ T coef_one();
+template <> __device__ __forceinline__ double coef_one<double>() { return 1.0; }
+template <> __device__ __forceinline__ float coef_one<float>() { return 1.0f; }
+template <> __device__ __forceinline__ double2 coef_one<double2>() { return make_double2(1.0, 0.0); }
+template <> __device__ __forceinline__ float2 coef_one<float2>() { return make_float2(1.0f, 0.0f); }
+
+// warp shuffles within segments of `w` lanes
+__device__ __forceinline__ double shfl_up(double v, int d, int w) { return __shfl_up_sync(0xffffffffu, v, d, w); }
+__device__ __forceinline__ float shfl_up(float v, int d, int w) { return __shfl_up_sync(0xffffffffu, v, d, w); }
+__device__ __forceinline__ double shfl_down(double v, int d, int w) { return __shfl_down_sync(0xffffffffu, v, d, w); }
+__device__ __forceinline__ float shfl_down(float v, int d, int w) { return __shfl_down_sync(0xffffffffu, v, d, w); }
+__device__ __forceinline__ double2 shfl_up(double2 v, int d, int w) { v.x = shfl_up(v.x, d, w); v.y = shfl_up(v.y, d, w); return v; }
+__device__ __forceinline__ float2 shfl_up(float2 v, int d, int w) { v.x = shfl_up(v.x, d, w); v.y = shfl_up(v.y, d, w); return v; }
+__device__ __forceinline__ double2 shfl_down(double2 v, int d, int w) { v.x = shfl_down(v.x, d, w); v.y = shfl_down(v.y, d, w); return v; }
+__device__ __forceinline__ float2 shfl_down(float2 v, int d, int w) { v.x = shfl_down(v.x, d, w); v.y = shfl_down(v.y, d, w); return v; }
+
+__device__ __forceinline__ void fsincos(double a, double *s, double *c) { sincos(a, s, c); }
+__device__ __forceinline__ void fsincos(float a, float *s, float *c) { sincosf(a, s, c); }
+__device__ __forceinline__ double fexpm1(double a) { return expm1(a); }
+__device__ __forceinline__ float fexpm1(float a) { return expm1f(a); }
+
+// ------------------------------------------------------------ DFT codelets
+// Forward transforms use w_N = exp(-2 pi i / N), inverse exp(+2 pi i / N),
+// both unnormalised.  The constants are cos / sin of multiples of 2 pi / N.
+#define DGPE_SQRT1_2 0.70710678118654752440
+#define DGPE_COS_PI8 0.92387953251128675613
+#define DGPE_SIN_PI8 0.38268343236508977173
+#define DGPE_SIN_2PI3 0.86602540378443864676
+#define DGPE_C1_5 0.30901699437494742410    /* cos(2 pi / 5) */
+#define DGPE_C2_5 (-0.80901699437494742410) /* cos(4 pi / 5) */
+#define DGPE_S1_5 0.95105651629515357212    /* sin(2 pi / 5) */
+#define DGPE_S2_5 0.58778525229247312917    /* sin(4 pi / 5) */
+
+// multiply by w_4 = -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot4(C a) {
+  C c;
+  if (INV) { c.x = -a.y; c.y = a.x; } else { c.x = a.y; c.y = -a.x; }
+  return c;
+}
+// multiply by w_16^k (k in 0..9); w_16^2 = w_8, w_16^4 = w_4
+template <bool INV, typename C> __device__ __forceinline__ C rot16(C a, int k) {
+  typedef decltype(a.x) R;
+  if (k == 0) return a;
+  if (k == 4) return rot4<INV>(a);
+  R c, s;  // forward angle -2 pi k / 16: w = c + i s
+  switch (k) {
+    case 1: c = (R)DGPE_COS_PI8; s = -(R)DGPE_SIN_PI8; break;
+    case 2: c = (R)DGPE_SQRT1_2; s = -(R)DGPE_SQRT1_2; break;
+    case 3: c = (R)DGPE_SIN_PI8; s = -(R)DGPE_COS_PI8; break;
+    case 6: c = -(R)DGPE_SQRT1_2; s = -(R)DGPE_SQRT1_2; break;
+    default: c = -(R)DGPE_COS_PI8; s = (R)DGPE_SIN_PI8; break;  // k = 9
+  }
+  if (INV) s = -s;
+  C r; r.x = a.x * c - a.y * s; r.y = a.x * s + a.y * c; return r;
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C *v) {
+  C t = v[0]; v[0] = t + v[1]; v[1] = t - v[1];
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft4s(C &a0, C &a1, C &a2, C &a3) {
+  C t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = rot4<INV>(a1 - a3);
+  a0 = t0 + t2; a2 = t0 - t2; a1 = t1 + t3; a3 = t1 - t3;
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C *v) { dft4s<INV>(v[0], v[1], v[2], v[3]); }
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C *v) {
+  // even/odd split: X[k] = E[k] + w8^k O[k], X[k+4] = E[k] - w8^k O[k]
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4s<INV>(e0, e1, e2, e3);
+  dft4s<INV>(o0, o1, o2, o3);
+  o1 = rot16<INV>(o1, 2);
+  o2 = rot4<INV>(o2);
+  o3 = rot16<INV>(o3, 6);
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C *v) {
+  // A_r[k] = DFT4_m(x[4m + r]);  X[k + 4s] = sum_r w4^{rs} (w16^{rk} A_r[k])
+#pragma unroll
+  for (int r = 0; r < 4; ++r) dft4s<INV>(v[r], v[r + 4], v[r + 8], v[r + 12]);
+  // now v[r + 4k] = A_r[k]
+#pragma unroll
+  for (int k = 1; k < 4; ++k)
+#pragma unroll
+    for (int r = 1; r < 4; ++r) v[r + 4 * k] = rot16<INV>(v[r + 4 * k], r * k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dft4s<INV>(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  // v[s + 4k] = X[k + 4s]: transpose the 4x4 block into natural order
+  C t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) v[k + 4 * s] = t[s + 4 * k];
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C *v) {
+  typedef decltype(v[0].x) R;
+  const R s3 = INV ? (R)DGPE_SIN_2PI3 : -(R)DGPE_SIN_2PI3;
+  C t = v[1] + v[2], u = v[1] - v[2];
+  C a; a.x = v[0].x - (R)0.5 * t.x; a.y = v[0].y - (R)0.5 * t.y;
+  C b; b.x = -s3 * u.y; b.y = s3 * u.x;  // i s3 u
+  v[0] = v[0] + t;
+  v[1] = a + b;
+  v[2] = a - b;
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft5(C *v) {
+  typedef decltype(v[0].x) R;
+  const R c1 = (R)DGPE_C1_5, c2 = (R)DGPE_C2_5;
+  const R s1 = INV ? (R)DGPE_S1_5 : -(R)DGPE_S1_5;
+  const R s2 = INV ? (R)DGPE_S2_5 : -(R)DGPE_S2_5;
+  C t1 = v[1] + v[4], t2 = v[2] + v[3], u1 = v[1] - v[4], u2 = v[2] - v[3];
+  C a1, a2, b1, b2;
+  a1.x = v[0].x + c1 * t1.x + c2 * t2.x; a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
+  a2.x = v[0].x + c2 * t1.x + c1 * t2.x; a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
+  // b1 = i (s1 u1 + s2 u2), b2 = i (s2 u1 - s1 u2)   (signs folded into s1, s2)
+  R p1x = s1 * u1.x + s2 * u2.x, p1y = s1 * u1.y + s2 * u2.y;
+  R p2x = s2 * u1.x - s1 * u2.x, p2y = s2 * u1.y - s1 * u2.y;
+  b1.x = -p1y; b1.y = p1x;
+  b2.x = -p2y; b2.y = p2x;
+  v[0] = v[0] + t1 + t2;
+  v[1] = a1 + b1; v[4] = a1 - b1;
+  v[2] = a2 + b2; v[3] = a2 - b2;
+}
+template <int RAD, bool INV, typename C> __device__ __forceinline__ void dft(C *v) {
+  if constexpr (RAD == 2) dft2<INV>(v);
+  else if constexpr (RAD == 3) dft3<INV>(v);
+  else if constexpr (RAD == 4) dft4<INV>(v);
+  else if constexpr (RAD == 5) dft5<INV>(v);
+  else if constexpr (RAD == 8) dft8<INV>(v);
+  else if constexpr (RAD == 16) dft16<INV>(v);
+}
+
+// ------------------------------------------------- Stockham FFT over a tile
+// Radix sequence of one line length (forward order; the inverse runs it
+// reversed so that its first stage reads what the forward's last wrote).
+struct FftPlan {
+  int n;
+  int ns;
+  int rad[10];
+};
+
+// One Stockham stage with radix RAD over `nlines` lines of length n held in
+// shared memory at sm[l*SL + a*SA].  Butterfly j of a line reads elements
+// j + r n/RAD, twiddles them by w_{Ns RAD}^{(j mod Ns) r}, applies the RAD-point
+// DFT and writes element (j / Ns) Ns RAD + (j mod Ns) + r Ns.  The first stage
+// reads through `load` instead of shared memory and the last writes through
+// `store` (its outputs are in natural order).  Each thread owns EPT / RAD
+// butterflies, so all of its values stay in registers across the barrier
+// that separates the reads from the writes (in-place update).
+template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, class Load, class Store>
+__device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines, int n, int Ns,
+                                          bool first, bool last, const cx<R> *__restrict__ tw,
+                                          Load &load, Store &store) {
+  static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
+  constexpr int NB = EPT / RAD;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int nbl = n / RAD;
+  const int B = nbl * nlines;
+  const int tstride = n / (Ns * RAD);
+  cx<R> v[EPT];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = t + i * T;
+    const bool ok = b < B;
+    const int l = LINE_FAST ? (b % nlines) : (b / nbl);
+    const int j = LINE_FAST ? (b / nlines) : (b % nbl);
+    cx<R> *u = v + i * RAD;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      const int a = j + r * nbl;
+      if (!ok) u[r] = czero<cx<R>>();
+      else if (first) u[r] = load(l, a);
+      else u[r] = sm[l * SL + a * SA];
+    }
+    if (!first) {
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        cx<R> w = tw[k * r * tstride];
+        u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
+      }
+    }
+    dft<RAD, INV>(u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = t + i * T;
+    if (b < B) {
+      const int l = LINE_FAST ? (b % nlines) : (b / nbl);
+      const int j = LINE_FAST ? (b / nlines) : (b % nbl);
+      const int base = (j / Ns) * Ns * RAD + (j % Ns);
+      cx<R> *u = v + i * RAD;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int a = base + r * Ns;
+        if (last) store(l, a, u[r]);
+        else sm[l * SL + a * SA] = u[r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Full transform of every line of the tile.  tw[t] = exp(-2 pi i t / n).
+template <typename R, int EPT, bool INV, bool LINE_FAST, class Load, class Store>
+__device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
+                         const cx<R> *__restrict__ tw, Load load, Store store) {
+  int Ns = 1;
+  for (int s = 0; s < pl.ns; ++s) {
+    const int rad = INV ? pl.rad[pl.ns - 1 - s] : pl.rad[s];
+    const bool first = (s == 0), last = (s == pl.ns - 1);
+    switch (rad) {
+      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 3: if constexpr (EPT % 3 == 0) fft_stage<R, EPT, 3, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 5: if constexpr (EPT % 5 == 0) fft_stage<R, EPT, 5, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      default: break;
+    }
+    Ns *= rad;
+  }
+}
+
+// ------------------------------------------- Crank-Nicolson (Thomas) solve
+// One CN substep along a line of n points, in increment form:
+//   x = psi + w,  A w = r,  r = -2 kt (2 psi_a - psi_{a-1} - psi_{a+1}),
+// A = I + kt T (kt = kappa tau), which equals A x = B psi with B = I - kt T.
+// LU of A: m_0 = 1/(1+2kt), m_a = 1/(1+2kt - kt^2 m_{a-1}), alpha_a = kt m_a;
+//   forward  y_a = alpha_a y_{a-1} + m_a r_a,
+//   backward w_a = y_a + alpha_a w_{a+1}.
+// Both first-order recurrences are split into TPL chunks of C points (one per
+// lane of a TPL-wide lane segment); chunk-local passes with zero inflow, a
+// Kogge-Stone scan of the chunk maps (P, Y) -> over the lanes, and a fix-up
+// with the in-chunk products P_a = prod_{b=a0..a} alpha_b and
+// Q_a = prod_{b=a..a0+C-1} alpha_b.  tab holds m, alpha, P, Q (n each).
+// The line lives in shared memory at line[a + a / C] (one pad per chunk keeps
+// the lane accesses on distinct banks).
+template <typename R, typename Coef, int CMAX>
+__device__ __forceinline__ void cn_line(cx<R> *line, int n, int C, int TPL, int q, Coef kt,
+                                        const Coef *__restrict__ tab, bool active) {
+  typedef cx<R> Cx;
+  const Coef *tm = tab, *ta = tab + n, *tp = tab + 2 * n, *tq = tab + 3 * n;
+  const int a0 = q * C;
+  Cx y[CMAX];
+  // right-hand side and chunk-local forward recurrence
+  Cx acc = czero<Cx>();
+  Cx prev = (active && a0 > 0) ? line[(a0 - 1) + (a0 - 1) / C] : czero<Cx>();
+  Cx cur = active ? line[a0 + a0 / C] : czero<Cx>();
+  const Coef m2kt = coef_scale(kt, (R)(-2));
+#pragma unroll
+  for (int i = 0; i < CMAX; ++i) {
+    if (i < C) {
+      const int a = a0 + i;
+      Cx nxt = (active && a + 1 < n) ? line[(a + 1) + (a + 1) / C] : czero<Cx>();
+      Cx lap = cur + cur - prev - nxt;
+      Cx r = coef_mul(m2kt, lap);
+      Coef ma = active ? tm[a] : coef_zero<Coef>(), al = active ? ta[a] : coef_zero<Coef>();
+      acc = coef_mul(al, acc) + coef_mul(ma, r);
+      y[i] = acc;
+      prev = cur;
+      cur = nxt;
+    }
+  }
+  // inclusive scan over the chunks (lane segment of width TPL)
+  Coef P = active ? tp[a0 + C - 1] : coef_zero<Coef>();
+  Cx Y = acc;
+  for (int d = 1; d < TPL; d <<= 1) {
+    Coef Pn = shfl_up(P, d, TPL);
+    Cx Yn = shfl_up(Y, d, TPL);
+    if (q >= d) { Y = Y + coef_mul(P, Yn); P = coef_prod(P, Pn); }
+  }
+  Cx yin = shfl_up(Y, 1, TPL);
+  if (q == 0) yin = czero<Cx>();
+#pragma unroll
+  for (int i = 0; i < CMAX; ++i)
+    if (i < C) y[i] = y[i] + coef_mul(active ? tp[a0 + i] : coef_zero<Coef>(), yin);
+  // chunk-local backward recurrence
+  acc = czero<Cx>();
+#pragma unroll
+  for (int i = CMAX - 1; i >= 0; --i) {
+    if (i < C) {
+      const int a = a0 + i;
+      Coef al = active ? ta[a] : coef_zero<Coef>();
+      acc = y[i] + coef_mul(al, acc);
+      y[i] = acc;
+    }
+  }
+  Coef Q = active ? tq[a0] : coef_zero<Coef>();
+  Cx W = acc;
+  for (int d = 1; d < TPL; d <<= 1) {
+    Coef Qn = shfl_down(Q, d, TPL);
+    Cx Wn = shfl_down(W, d, TPL);
+    if (q + d < TPL) { W = W + coef_mul(Q, Wn); Q = coef_prod(Q, Qn); }
+  }
+  Cx win = shfl_down(W, 1, TPL);
+  if (q == TPL - 1) win = czero<Cx>();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < CMAX; ++i)
+      if (i < C) {
+        const int a = a0 + i;
+        Cx w = y[i] + coef_mul(tq[a], win);
+        const int ia = a + a / C;
+        line[ia] = line[ia] + w;
+      }
+  }
+}
+
+// --------------------------------------------------- FP64 block reductions
+// Deterministic for a fixed block size: warp tree, then warp totals in order.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+// Returns the block total in thread 0 (other threads: unspecified).
+__device__ __forceinline__ double block_sum(double v, double *red /* >= 32 */) {
+  const int t = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (t == 0)
+    for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+}  // namespace dgpe

@@ -1,0 +1,624 @@
+// dgpe_engine.cuh -- host runtime of one solver: FP64 precompute of the
+// tables (dipolar kernel U(k)/N, Crank-Nicolson LU and scan tables, FFT
+// roots, trap potential), pass configuration, launch sequence and CUDA-graph
+// capture.  Instantiated for double (FP64 form) and float (FP32-bulk form).
+#pragma once
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dgpe.h"
+#include "dgpe_kernels.cuh"
+
+namespace dgpe {
+
+typedef std::complex<double> zd;
+
+// Engine interface used by the C ABI.
+struct Engine {
+  virtual ~Engine() {}
+  virtual int init(const dgpe_params &p, cudaStream_t user) = 0;
+  virtual int set_psi_device(const void *src, int fp64, cudaStream_t s) = 0;
+  virtual int get_psi_device(void *dst, int fp64, cudaStream_t s) = 0;
+  virtual int set_psi_host(const double *src, cudaStream_t s) = 0;
+  virtual int get_psi_host(double *dst, cudaStream_t s) = 0;
+  virtual int step(int n, cudaStream_t s) = 0;
+  virtual int observables(dgpe_obs *o, cudaStream_t s) = 0;
+  virtual int dipolar_potential(double *phi_host, cudaStream_t s) = 0;
+  virtual int set_g(double g, cudaStream_t s) = 0;
+  virtual int set_mode(int mode, cudaStream_t s) = 0;
+  virtual int set_modulation(const double *c, int M, cudaStream_t s) = 0;
+  virtual int set_time(long long step, cudaStream_t s) = 0;
+  virtual int get_time(long long *step, cudaStream_t s) = 0;
+  virtual int launches_per_step() const = 0;
+  virtual size_t sites() const = 0;
+  std::string err;
+};
+
+Engine *make_engine_f64();
+Engine *make_engine_f32();
+
+// ----------------------------------------------------------- host helpers
+// Radix sequence for length n whose radices divide ept (largest first).
+inline bool make_plan(int n, int ept, FftPlan &pl) {
+  static const int cand[6] = {16, 8, 5, 4, 3, 2};
+  pl.n = n;
+  pl.ns = 0;
+  int m = n;
+  for (int ci = 0; ci < 6; ++ci) {
+    const int R = cand[ci];
+    while (m % R == 0 && ept % R == 0) {
+      if (pl.ns >= 10) return false;
+      pl.rad[pl.ns++] = R;
+      m /= R;
+    }
+  }
+  return m == 1 && pl.ns > 0;
+}
+
+// erfcx(u) = exp(u^2) erfc(u) for u >= 0; continued asymptotic series where
+// erfc underflows.
+inline double host_erfcx(double u) {
+  if (u < 25.0) return std::exp(u * u) * std::erfc(u);
+  const double u2 = u * u;
+  double term = 1.0, sum = 1.0;
+  for (int m = 1; m < 8; ++m) {
+    term *= -(2.0 * m - 1.0) / (2.0 * u2);
+    sum += term;
+  }
+  return sum / (u * std::sqrt(M_PI));
+}
+
+inline double wavenumber(int j, int n, double h) {
+  const int jj = (j <= n / 2) ? j : j - n;
+  return 2.0 * M_PI * (double)jj / ((double)n * h);
+}
+
+#define DGPE_CK(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return (e_ == cudaErrorMemoryAllocation) ? DGPE_ENOMEM : DGPE_ECUDA;   \
+    }                                                                        \
+  } while (0)
+
+template <typename R> struct EngineT : Engine {
+  typedef cx<R> Cx;
+  static constexpr int EPT_X = 8;                  // x-pass elements per thread
+  static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFT passes
+  static constexpr int CMAX = 16;                  // CN chunk length bound
+  static constexpr int W = 128 / (int)sizeof(Cx);  // columns per strided tile (128 B)
+
+  dgpe_params p{};
+  int dim = 3, nx = 0, ny = 0, nz = 1, nrows = 0, px = 0, ncol_spec = 0;
+  size_t nsites = 0, nspec = 0;
+  bool has_dip = false;
+  int imag = 1;
+
+  Cx *psi = nullptr, *spec = nullptr;
+  R *U = nullptr, *phi_tmp = nullptr;
+  Cx *tw[3] = {nullptr, nullptr, nullptr};
+  R *vt[3] = {nullptr, nullptr, nullptr};
+  void *cntab[3] = {nullptr, nullptr, nullptr};
+  double *prm = nullptr, *partial = nullptr, *obs_part = nullptr, *dip_part = nullptr, *obs_out = nullptr;
+  double2 *stage = nullptr;  // FP64 staging buffer for host transfers (lazy)
+  long long *dstep = nullptr;
+  unsigned *counter = nullptr;
+  FftPlan plx{}, ply{}, plz{}, plx_s{};
+  double tau[3] = {0, 0, 0};
+
+  // pass configurations
+  int x_LP = 0, x_T = 0, x_TPL = 0, x_C = 0, x_pitchz = 0, x_pitch = 0, x_grid = 0;
+  size_t x_smem = 0;
+  struct CnCfg { int n, ncols, W, TPL, C, pitch, T; long long es, os; dim3 grid; size_t smem; };
+  CnCfg cn[3];   // index = axis (0 unused: x is fused into P1)
+  struct FtCfg { int n, T; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
+  FtCfg fy{}, fz{};
+  int obs_rows = 1, obs_blocks = 0, ndip = 0;
+
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool use_graph = true;
+
+  ~EngineT() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    void *bufs[] = {psi, spec, U, phi_tmp, tw[0], tw[1], tw[2], vt[0], vt[1], vt[2],
+                    cntab[0], cntab[1], cntab[2], prm, partial, obs_part, dip_part, obs_out,
+                    dstep, counter, stage};
+    for (void *b : bufs)
+      if (b) cudaFree(b);
+  }
+
+  size_t sites() const override { return nsites; }
+
+  int launches_per_step() const override {
+    int k = 1 + (dim == 3 ? 2 : 1);  // P1, CN passes
+    if (has_dip) k += (dim == 3 ? 4 : 2);
+    return k;
+  }
+
+  template <typename T> int dalloc(T **ptr, size_t count) {
+    DGPE_CK(cudaMalloc((void **)ptr, sizeof(T) * (count ? count : 1)));
+    return DGPE_OK;
+  }
+  template <typename T> int upload(T *dst, const std::vector<T> &src) {
+    DGPE_CK(cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return DGPE_OK;
+  }
+
+  // ---------------------------------------------------------------- init
+  int init(const dgpe_params &pin, cudaStream_t user) override {
+    p = pin;
+    dim = p.dim;
+    nx = p.n[0];
+    ny = p.n[1];
+    nz = (dim == 3) ? p.n[2] : 1;
+    nrows = ny * nz;
+    nsites = (size_t)nx * ny * nz;
+    imag = (p.mode == DGPE_IMAG);
+    has_dip = (p.kernel != DGPE_KERNEL_NONE);
+    px = nx / 2 + 1;
+    if (sizeof(Cx) == 8) px = (px + 1) & ~1;  // 16-byte rows for FP32 complex
+    ncol_spec = nx / 2 + 1;
+    nspec = (size_t)px * nrows;
+
+    // FFT plans
+    if (!make_plan(nx, EPT_X, plx) || !make_plan(ny, EPT_S, ply) ||
+        (dim == 3 && !make_plan(nz, EPT_S, plz))) {
+      err = "grid size not supported by the FFT plans (use powers of two 16..512)";
+      return DGPE_EUNSUPPORTED;
+    }
+    int rc;
+    if ((rc = dalloc(&psi, nsites))) return rc;
+    DGPE_CK(cudaMemset(psi, 0, sizeof(Cx) * nsites));
+    if (has_dip && (rc = dalloc(&spec, nspec))) return rc;
+    if ((rc = dalloc(&prm, PRM_COUNT))) return rc;
+    if ((rc = dalloc(&dstep, 1))) return rc;
+    if ((rc = dalloc(&counter, 1))) return rc;
+    DGPE_CK(cudaMemset(dstep, 0, sizeof(long long)));
+    DGPE_CK(cudaMemset(counter, 0, sizeof(unsigned)));
+    std::vector<double> hp(PRM_COUNT, 0.0);
+    hp[PRM_SC] = 1.0;
+    hp[PRM_DT] = p.dt;
+    hp[PRM_G] = p.g;
+    hp[PRM_GDD] = p.gdd;
+    hp[PRM_CELL] = p.h[0] * p.h[1] * (dim == 3 ? p.h[2] : 1.0);
+    if ((rc = upload(prm, hp))) return rc;
+
+    // twiddles and potential tables
+    const int ns[3] = {nx, ny, nz};
+    for (int a = 0; a < dim; ++a) {
+      std::vector<Cx> w(ns[a]);
+      for (int t = 0; t < ns[a]; ++t) {
+        const double ang = -2.0 * M_PI * (double)t / (double)ns[a];
+        w[t].x = (R)std::cos(ang);
+        w[t].y = (R)std::sin(ang);
+      }
+      if ((rc = dalloc(&tw[a], ns[a]))) return rc;
+      if ((rc = upload(tw[a], w))) return rc;
+    }
+    for (int a = 0; a < 3; ++a) {
+      const int n = (a < dim) ? ns[a] : 1;
+      std::vector<R> v(n, (R)0);
+      if (a < dim)
+        for (int i = 0; i < n; ++i) {
+          const double x = ((double)i - (double)(n / 2)) * p.h[a];
+          v[i] = (R)(0.5 * p.nu[a] * p.nu[a] * x * x);
+        }
+      if ((rc = dalloc(&vt[a], n))) return rc;
+      if ((rc = upload(vt[a], v))) return rc;
+    }
+    if (has_dip && (rc = build_kernel_table())) return rc;
+
+    // configurations
+    x_C = CMAX;
+    if (nx % x_C) { err = "nx must be a multiple of 16"; return DGPE_EUNSUPPORTED; }
+    x_TPL = nx / x_C;
+    if (x_TPL > 32) { err = "nx > 512 not supported"; return DGPE_EUNSUPPORTED; }
+    x_LP = std::max(1, 128 / x_TPL);
+    x_T = 2 * x_LP * x_TPL;
+    x_pitchz = nx + 1;
+    x_pitch = nx + nx / x_C + 1;
+    x_smem = sizeof(Cx) * (size_t)std::max(x_LP * x_pitchz, 2 * x_LP * x_pitch);
+    {
+      const int npairs = (nrows + 1) / 2;
+      x_grid = (npairs + x_LP - 1) / x_LP;
+    }
+    if ((rc = make_cn_cfg(1))) return rc;
+    if (dim == 3 && (rc = make_cn_cfg(2))) return rc;
+    if ((rc = build_cn_tables())) return rc;
+    fy.axis = 1;
+    fz.axis = 2;
+    if (has_dip) {
+      // y transform over the spectrum
+      fy.n = ny; fy.T = W * ny / EPT_S; fy.es = px; fy.os = (long long)ny * px;
+      fy.grid = dim3((ncol_spec + W - 1) / W, nz); fy.smem = sizeof(Cx) * (size_t)ny * W; fy.pl = ply;
+      if (dim == 3) {
+        fz.n = nz; fz.T = W * nz / EPT_S; fz.es = (long long)ny * px; fz.os = px;
+        fz.grid = dim3((ncol_spec + W - 1) / W, ny); fz.smem = sizeof(Cx) * (size_t)nz * W; fz.pl = plz;
+      }
+      if (fy.T > 1024 || fz.T > 1024) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
+    }
+    // scratch: norm partials, observable partials
+    obs_rows = std::max(1, (int)(((size_t)nrows + 4095) / 4096));
+    obs_blocks = (nrows + obs_rows - 1) / obs_rows;
+    const FtCfg &last = (dim == 3) ? fz : fy;
+    ndip = has_dip ? (int)(last.grid.x * last.grid.y) : 0;
+    const CnCfg &fin = cn[dim == 3 ? 2 : 1];
+    if ((rc = dalloc(&partial, (size_t)fin.grid.x * fin.grid.y))) return rc;
+    if ((rc = dalloc(&obs_part, (size_t)obs_blocks * OBS_COUNT))) return rc;
+    if ((rc = dalloc(&dip_part, (size_t)std::max(ndip, 1)))) return rc;
+    if ((rc = dalloc(&obs_out, OBS_COUNT + 1))) return rc;
+    if ((rc = set_smem_attrs())) return rc;
+    DGPE_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    use_graph = !(p.flags & DGPE_FLAG_NO_GRAPH);
+    if (use_graph && (rc = capture())) return rc;
+    (void)user;
+    return DGPE_OK;
+  }
+
+  int make_cn_cfg(int axis) {
+    CnCfg &c = cn[axis];
+    const int n = (axis == 1) ? ny : nz;
+    c.n = n;
+    c.ncols = nx;
+    c.W = W;
+    int tpl = 32;
+    while (tpl > 1 && (n % tpl || n / tpl < 1)) tpl >>= 1;
+    c.TPL = tpl;
+    c.C = n / tpl;
+    if (c.C > CMAX) { err = "line too long for the CN chunking"; return DGPE_EUNSUPPORTED; }
+    c.pitch = n + n / c.C + 1;
+    c.T = W * tpl;
+    if (axis == 1) { c.es = nx; c.os = (long long)nx * ny; c.grid = dim3((nx + W - 1) / W, nz); }
+    else { c.es = (long long)nx * ny; c.os = nx; c.grid = dim3((nx + W - 1) / W, ny); }
+    c.smem = sizeof(Cx) * (size_t)W * c.pitch;
+    return DGPE_OK;
+  }
+
+  // U(k)/N on the half spectrum [z][y][kx], FP64 then rounded to R.
+  int build_kernel_table() {
+    std::vector<R> hu(nspec, (R)0);
+    const double N = (double)nsites;
+    for (int kz = 0; kz < nz; ++kz)
+      for (int ky = 0; ky < ny; ++ky)
+        for (int kx = 0; kx < ncol_spec; ++kx) {
+          const double qx = wavenumber(kx, nx, p.h[0]), qy = wavenumber(ky, ny, p.h[1]);
+          double u;
+          if (dim == 3) {
+            const double qz = wavenumber(kz, nz, p.h[2]);
+            const double k2 = qx * qx + qy * qy + qz * qz;
+            u = (k2 == 0.0) ? 0.0 : (4.0 * M_PI / 3.0) * (3.0 * qz * qz / k2 - 1.0);
+          } else {
+            // dipoles along z, Gaussian z-profile exp(-z^2/d^2)/(sqrt(pi) d):
+            // U2 = (4pi/3)/(sqrt(2pi) d) [2 - 3 sqrt(pi/2) q erfcx(q/sqrt2)], q = k d
+            const double d = p.qd, q = std::sqrt(qx * qx + qy * qy) * d;
+            u = (4.0 * M_PI / 3.0) / (std::sqrt(2.0 * M_PI) * d) *
+                (2.0 - 3.0 * std::sqrt(M_PI / 2.0) * q * host_erfcx(q / std::sqrt(2.0)));
+          }
+          hu[((size_t)kz * ny + ky) * px + kx] = (R)(u / N);
+        }
+    int rc;
+    if ((rc = dalloc(&U, nspec))) return rc;
+    return upload(U, hu);
+  }
+
+  // Crank-Nicolson LU and chunk-scan tables for axis a: m, alpha, P, Q.
+  int build_cn_tables() {
+    const int ns[3] = {nx, ny, nz};
+    const int Cs[3] = {x_C, cn[1].C, dim == 3 ? cn[2].C : 1};
+    for (int a = 0; a < dim; ++a) {
+      const int n = ns[a], C = Cs[a];
+      tau[a] = p.dt / (4.0 * p.h[a] * p.h[a]);
+      const zd kt = imag ? zd(tau[a], 0.0) : zd(0.0, tau[a]);
+      std::vector<zd> m(n), al(n), P(n), Q(n);
+      const zd b = 1.0 + 2.0 * kt;
+      m[0] = 1.0 / b;
+      for (int i = 1; i < n; ++i) m[i] = 1.0 / (b - kt * kt * m[i - 1]);
+      for (int i = 0; i < n; ++i) al[i] = kt * m[i];
+      for (int c0 = 0; c0 < n; c0 += C) {
+        zd pr = 1.0;
+        for (int i = c0; i < c0 + C; ++i) { pr *= al[i]; P[i] = pr; }
+        pr = 1.0;
+        for (int i = c0 + C - 1; i >= c0; --i) { pr *= al[i]; Q[i] = pr; }
+      }
+      if (!cntab[a]) {
+        int rc = dalloc((Cx **)&cntab[a], 4 * (size_t)n);
+        if (rc) return rc;
+      }
+      if (imag) {
+        std::vector<R> t(4 * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+          t[i] = (R)m[i].real(); t[n + i] = (R)al[i].real();
+          t[2 * n + i] = (R)P[i].real(); t[3 * n + i] = (R)Q[i].real();
+        }
+        DGPE_CK(cudaMemcpy(cntab[a], t.data(), sizeof(R) * t.size(), cudaMemcpyHostToDevice));
+      } else {
+        std::vector<Cx> t(4 * (size_t)n);
+        auto put = [&](size_t i, zd v) { t[i].x = (R)v.real(); t[i].y = (R)v.imag(); };
+        for (int i = 0; i < n; ++i) {
+          put(i, m[i]); put(n + i, al[i]); put(2 * n + i, P[i]); put(3 * n + i, Q[i]);
+        }
+        DGPE_CK(cudaMemcpy(cntab[a], t.data(), sizeof(Cx) * t.size(), cudaMemcpyHostToDevice));
+      }
+    }
+    return DGPE_OK;
+  }
+
+  template <typename K> int smem_attr(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024)
+      DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return DGPE_OK;
+  }
+  int set_smem_attrs() {
+    int rc;
+    if ((rc = smem_attr(k_dens_r2c_x<R, EPT_X>, x_smem))) return rc;
+    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0>, x_smem))) return rc;
+    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0>, x_smem))) return rc;
+    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1>, x_smem))) return rc;
+    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 1>, x_smem))) return rc;
+    const size_t fs = std::max(fy.smem, fz.smem);
+    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 0>, fs))) return rc;
+    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 1>, fs))) return rc;
+    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 2>, fs))) return rc;
+    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 3>, fs))) return rc;
+    const size_t cs = std::max(cn[1].smem, dim == 3 ? cn[2].smem : 0);
+    if ((rc = smem_attr(k_cn_strided<R, R, CMAX>, cs))) return rc;
+    if ((rc = smem_attr(k_cn_strided<R, Cx, CMAX>, cs))) return rc;
+    return DGPE_OK;
+  }
+
+  // ------------------------------------------------------------- launches
+  XArgs<R> xargs() const {
+    XArgs<R> A{};
+    A.psi = psi; A.spec = spec; A.phi_out = phi_tmp; A.prm = prm; A.step = dstep;
+    A.tw = tw[0]; A.vx = vt[0]; A.vy = vt[1]; A.vz = vt[2]; A.cntab = cntab[0];
+    A.pl = plx; A.nx = nx; A.ny = ny; A.nrows = nrows; A.px = px; A.LP = x_LP;
+    A.pitchz = x_pitchz; A.pitch = x_pitch; A.TPL = x_TPL; A.C = x_C;
+    A.imag = imag; A.has_dip = has_dip ? 1 : 0; A.tau = tau[0];
+    return A;
+  }
+  SArgs<R> sargs(const FtCfg &f) const {
+    SArgs<R> A{};
+    A.spec = spec; A.U = U; A.partial = dip_part; A.tw = tw[f.axis]; A.pl = f.pl;
+    A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = W; A.nxh = nx / 2;
+    return A;
+  }
+  int launch_fft(const FtCfg &f, int mode, cudaStream_t s) {
+    SArgs<R> A = sargs(f);
+    switch (mode) {
+      case 0: k_fft_strided<R, EPT_S, 0><<<f.grid, f.T, f.smem, s>>>(A); break;
+      case 1: k_fft_strided<R, EPT_S, 1><<<f.grid, f.T, f.smem, s>>>(A); break;
+      case 2: k_fft_strided<R, EPT_S, 2><<<f.grid, f.T, f.smem, s>>>(A); break;
+      default: k_fft_strided<R, EPT_S, 3><<<f.grid, f.T, f.smem, s>>>(A); break;
+    }
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  int launch_cn(int axis, bool final_pass, cudaStream_t s) {
+    const CnCfg &c = cn[axis];
+    CArgs<R> A{};
+    A.psi = psi; A.cntab = cntab[axis]; A.prm = prm; A.partial = partial; A.counter = counter;
+    A.step = dstep; A.estride = c.es; A.ostride = c.os; A.n = c.n; A.ncols = c.ncols; A.W = c.W;
+    A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
+    A.norm = (final_pass && imag) ? 1 : 0; A.tau = tau[axis];
+    if (imag) k_cn_strided<R, R, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
+    else k_cn_strided<R, Cx, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  int launch_forward_spectrum(cudaStream_t s) {  // density -> spectrum (x, y)
+    XArgs<R> A = xargs();
+    k_dens_r2c_x<R, EPT_X><<<x_grid, x_T, x_smem, s>>>(A);
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  int launch_p1(int mode, cudaStream_t s) {
+    XArgs<R> A = xargs();
+    if (mode == 0) {
+      if (imag) k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
+      else k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
+    } else {
+      k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1><<<x_grid, x_T, x_smem, s>>>(A);
+    }
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  // Phi_d chain up to (not including) the C2R along x.
+  int launch_dipolar_chain(cudaStream_t s) {
+    int rc;
+    if ((rc = launch_forward_spectrum(s))) return rc;
+    if (dim == 3) {
+      if ((rc = launch_fft(fy, 0, s))) return rc;
+      if ((rc = launch_fft(fz, 2, s))) return rc;
+      if ((rc = launch_fft(fy, 1, s))) return rc;
+    } else {
+      if ((rc = launch_fft(fy, 2, s))) return rc;
+    }
+    return DGPE_OK;
+  }
+  int launch_step(cudaStream_t s) {
+    int rc;
+    if (has_dip && (rc = launch_dipolar_chain(s))) return rc;
+    if ((rc = launch_p1(0, s))) return rc;
+    if ((rc = launch_cn(1, dim == 2, s))) return rc;
+    if (dim == 3 && (rc = launch_cn(2, true, s))) return rc;
+    return DGPE_OK;
+  }
+  int capture() {
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+    DGPE_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) { err = std::string("graph capture: ") + cudaGetErrorString(e); return DGPE_ECUDA; }
+    graph = g;
+    DGPE_CK(cudaGraphInstantiate(&gexec, graph, 0));
+    return DGPE_OK;
+  }
+
+  // ------------------------------------------------------------ API calls
+  int step(int n, cudaStream_t s) override {
+    for (int i = 0; i < n; ++i) {
+      if (use_graph) DGPE_CK(cudaGraphLaunch(gexec, s));
+      else {
+        int rc = launch_step(s);
+        if (rc) return rc;
+      }
+    }
+    return DGPE_OK;
+  }
+  int reset_scale(cudaStream_t s) {
+    const double one = 1.0, zero = 0.0;
+    DGPE_CK(cudaMemcpyAsync(prm + PRM_SC, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaMemcpyAsync(prm + PRM_NONFINITE, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int set_psi_host(const double *src, cudaStream_t s) override {
+    if (!stage) { int rc = dalloc(&stage, nsites); if (rc) return rc; }
+    DGPE_CK(cudaMemcpyAsync(stage, src, sizeof(double2) * nsites, cudaMemcpyHostToDevice, s));
+    return set_psi_device(stage, 1, s);
+  }
+  int get_psi_host(double *dst, cudaStream_t s) override {
+    if (!stage) { int rc = dalloc(&stage, nsites); if (rc) return rc; }
+    int rc = get_psi_device(stage, 1, s);
+    if (rc) return rc;
+    DGPE_CK(cudaMemcpyAsync(dst, stage, sizeof(double2) * nsites, cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int set_psi_device(const void *src, int fp64, cudaStream_t s) override {
+    const int blocks = 152 * 8;
+    if (fp64) k_import<R, double2><<<blocks, 256, 0, s>>>(psi, (const double2 *)src, nsites);
+    else k_import<R, float2><<<blocks, 256, 0, s>>>(psi, (const float2 *)src, nsites);
+    DGPE_CK(cudaGetLastError());
+    int rc = reset_scale(s);
+    if (rc) return rc;
+    return set_time(0, s);
+  }
+  int get_psi_device(void *dst, int fp64, cudaStream_t s) override {
+    const int blocks = 152 * 8;
+    if (fp64) k_export<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, psi, prm, nsites);
+    else k_export<R, float2><<<blocks, 256, 0, s>>>((float2 *)dst, psi, prm, nsites);
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  int observables(dgpe_obs *o, cudaStream_t s) override {
+    int rc;
+    if (has_dip) {
+      if ((rc = launch_forward_spectrum(s))) return rc;
+      if (dim == 3) {
+        if ((rc = launch_fft(fy, 0, s))) return rc;
+        if ((rc = launch_fft(fz, 3, s))) return rc;
+      } else {
+        if ((rc = launch_fft(fy, 3, s))) return rc;
+      }
+    }
+    OArgs<R> A{};
+    A.psi = psi; A.prm = prm; A.partial = obs_part; A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
+    A.rows_per_block = obs_rows; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
+    A.nux = p.nu[0]; A.nuy = p.nu[1]; A.nuz = (dim == 3) ? p.nu[2] : 0.0;
+    k_obs_sites<R><<<obs_blocks, 256, 0, s>>>(A);
+    DGPE_CK(cudaGetLastError());
+    k_obs_final<<<1, 256, 0, s>>>(obs_part, obs_blocks, dip_part, ndip, obs_out);
+    DGPE_CK(cudaGetLastError());
+    double h[OBS_COUNT + 1];
+    double hp[PRM_COUNT];
+    long long st = 0;
+    DGPE_CK(cudaMemcpyAsync(h, obs_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaMemcpyAsync(hp, prm, sizeof(hp), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaMemcpyAsync(&st, dstep, sizeof(st), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    if (h[OBS_BAD] > 0.0 || hp[PRM_NONFINITE] != 0.0) {
+      err = "state holds NaN or Inf";
+      return DGPE_ENONFINITE;
+    }
+    const double cell = hp[PRM_CELL];
+    const double t = (double)st * p.dt;
+    double sm = 1.0;
+    for (int m = 1; m <= (int)hp[PRM_M]; ++m) sm += hp[PRM_CM + m - 1] * std::sin((double)m * t);
+    const double norm = cell * h[OBS_N];
+    double kin = 0.5 * cell * (h[OBS_KX] / (p.h[0] * p.h[0]) + h[OBS_KY] / (p.h[1] * p.h[1]));
+    if (dim == 3) kin += 0.5 * cell * h[OBS_KZ] / (p.h[2] * p.h[2]);
+    const double pot = sm * cell * h[OBS_V];
+    const double con = hp[PRM_G] * cell * h[OBS_N2];
+    const double dip = has_dip ? hp[PRM_GDD] * cell * h[OBS_COUNT] : 0.0;
+    o->norm = norm;
+    o->kin = kin / norm;
+    o->pot = pot / norm;
+    o->contact = con / norm;
+    o->dipolar = dip / norm;
+    o->mu = (kin + pot + con + dip) / norm;
+    o->energy = (kin + pot + 0.5 * con + 0.5 * dip) / norm;
+    o->rms[0] = std::sqrt(h[OBS_X2] / h[OBS_N]);
+    o->rms[1] = std::sqrt(h[OBS_Y2] / h[OBS_N]);
+    o->rms[2] = (dim == 3) ? std::sqrt(h[OBS_Z2] / h[OBS_N]) : 0.0;
+    o->rms_r = std::sqrt((h[OBS_X2] + h[OBS_Y2] + h[OBS_Z2]) / h[OBS_N]);
+    o->t = t;
+    if (!std::isfinite(o->mu) || !std::isfinite(norm)) { err = "non-finite observables"; return DGPE_ENONFINITE; }
+    return DGPE_OK;
+  }
+  int dipolar_potential(double *phi_host, cudaStream_t s) override {
+    std::vector<R> tmp(nsites, (R)0);
+    if (has_dip) {
+      if (!phi_tmp) { int rc = dalloc(&phi_tmp, nsites); if (rc) return rc; }
+      int rc;
+      if ((rc = launch_dipolar_chain(s))) return rc;
+      if ((rc = launch_p1(1, s))) return rc;
+      DGPE_CK(cudaMemcpyAsync(tmp.data(), phi_tmp, sizeof(R) * nsites, cudaMemcpyDeviceToHost, s));
+      DGPE_CK(cudaStreamSynchronize(s));
+    }
+    for (size_t i = 0; i < nsites; ++i) phi_host[i] = (double)tmp[i];
+    return DGPE_OK;
+  }
+  int set_g(double g, cudaStream_t s) override {
+    p.g = g;
+    DGPE_CK(cudaMemcpyAsync(prm + PRM_G, &p.g, sizeof(double), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int set_mode(int mode, cudaStream_t s) override {
+    if (mode != DGPE_IMAG && mode != DGPE_REAL) { err = "bad mode"; return DGPE_EINVAL; }
+    // fold the lazy scale into psi, then rebuild the CN tables and the graph
+    k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, nsites);
+    DGPE_CK(cudaGetLastError());
+    int rc = reset_scale(s);
+    if (rc) return rc;
+    p.mode = mode;
+    imag = (mode == DGPE_IMAG);
+    if ((rc = build_cn_tables())) return rc;
+    if (use_graph && (rc = capture())) return rc;
+    return DGPE_OK;
+  }
+  int set_modulation(const double *c, int M, cudaStream_t s) override {
+    if (M < 0 || M > 16 || (M > 0 && !c)) { err = "M must be 0..16"; return DGPE_EINVAL; }
+    double h[17] = {0};
+    h[0] = (double)M;
+    for (int i = 0; i < M; ++i) h[1 + i] = c[i];
+    DGPE_CK(cudaMemcpyAsync(prm + PRM_M, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int set_time(long long st, cudaStream_t s) override {
+    DGPE_CK(cudaMemcpyAsync(dstep, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int get_time(long long *st, cudaStream_t s) override {
+    DGPE_CK(cudaMemcpyAsync(st, dstep, sizeof(*st), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+};
+
+}  // namespace dgpe

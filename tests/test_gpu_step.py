@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances: relative L2 of psi <= 1e-10 for the FP64 form and <= 1e-5 for the
+FP32-bulk form; mu and energy within 1e-11 (FP64) and 1e-6 (FP32-bulk),
+relative.  Shorter runs are held to the same bounds (they are upper bounds;
+the measured errors are printed)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_04640_gb300 import build as gbuild
+from paper_1601_04640_gb300 import dgpe, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_PSI = {True: 1e-10, False: 1e-5}
+TOL_MU = {True: 1e-11, False: 1e-6}
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    gbuild.build()
+    oracle.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def make_case(dim, n, h, nu, g, gdd, dt, imag, kernel=None, seed=1601, noise=0.01, widths=None):
+    kname = {None: "dipolar3d" if dim == 3 else "quasi2d", "none": "none"}[kernel]
+    op = oracle.Params(dim=dim, n=n, h=h, nu=nu, g=g, gdd=gdd, dt=dt, imag=imag, kernel=kname, qd=0.5)
+    kc = {None: None, "none": dgpe.DGPE_KERNEL_NONE}[kernel]
+    psi0 = synth.gaussian_state(n, h, widths or nu, noise, seed)
+    return op, kc, psi0
+
+
+def gpu_run(dim, n, h, nu, g, gdd, dt, imag, fp64, kc, psi0, steps, graph=True):
+    with dgpe.Solver(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel=kc, graph=graph) as s:
+        s.set_psi(psi0)
+        s.step(steps)
+        return s.get_psi(), s.observables()
+
+
+CASES_3D = [
+    ((32, 32, 32), (0.25, 0.25, 0.25), (1.0, 1.0, 2.0)),
+    ((64, 32, 16), (0.2, 0.3, 0.45), (1.0, 1.3, 0.8)),
+]
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("case", range(len(CASES_3D)))
+def test_dipolar_potential_3d(fp64, case):
+    n, h, nu = CASES_3D[case]
+    op, kc, psi0 = make_case(3, n, h, nu, 10, 5, 1e-3, False)
+    with dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, False, fp64) as s:
+        s.set_psi(psi0)
+        phi = s.dipolar_potential()
+    ref = oracle.dipolar_potential(op, np.abs(psi0) ** 2)
+    err = np.max(np.abs(phi - ref)) / np.max(np.abs(ref))
+    print("phi rel max err", err)
+    assert err < (1e-12 if fp64 else 2e-6)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_dipolar_potential_quasi2d(fp64):
+    n, h, nu = (64, 32), (0.2, 0.3), (1.0, 1.5)
+    op, kc, psi0 = make_case(2, n, h, nu, 10, 5, 1e-3, False)
+    with dgpe.Solver(2, n, h, nu, 10, 5, 1e-3, False, fp64) as s:
+        s.set_psi(psi0)
+        phi = s.dipolar_potential()
+    ref = oracle.dipolar_potential(op, np.abs(psi0) ** 2)
+    err = np.max(np.abs(phi - ref)) / np.max(np.abs(ref))
+    print("phi rel max err", err)
+    assert err < (1e-12 if fp64 else 2e-6)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("case", range(len(CASES_3D)))
+def test_step_parity_3d(fp64, imag, case):
+    n, h, nu = CASES_3D[case]
+    op, kc, psi0 = make_case(3, n, h, nu, 50.0, 15.0, 2e-3, imag)
+    for steps in (1, 10):
+        psi, obs = gpu_run(3, n, h, nu, 50.0, 15.0, 2e-3, imag, fp64, kc, psi0, steps)
+        ref = oracle.step(op, psi0, 0, steps)
+        e = rel_l2(psi, ref)
+        print("steps", steps, "rel L2", e)
+        assert e < TOL_PSI[fp64]
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("imag", [True, False])
+def test_step_parity_2d(fp64, imag):
+    n, h, nu = (64, 32), (0.2, 0.3), (1.0, 1.5)
+    op, kc, psi0 = make_case(2, n, h, nu, 80.0, 40.0, 1e-3, imag)
+    psi, obs = gpu_run(2, n, h, nu, 80.0, 40.0, 1e-3, imag, fp64, kc, psi0, 10)
+    ref = oracle.step(op, psi0, 0, 10)
+    e = rel_l2(psi, ref)
+    print("rel L2", e)
+    assert e < TOL_PSI[fp64]
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("imag", [True, False])
+def test_cn_only(fp64, imag):
+    """g = g_dd = 0, no trap: the exponential is the identity and the step is
+    the three CN substeps alone (large dt so the solves are far from I)."""
+    n, h = (32, 64, 16), (0.2, 0.15, 0.3)
+    op, kc, psi0 = make_case(3, n, h, (0, 0, 0), 0, 0, 0.05, imag, kernel="none", noise=0.3,
+                             widths=(1.0, 1.0, 1.0))
+    psi, _ = gpu_run(3, n, h, (0, 0, 0), 0, 0, 0.05, imag, fp64, kc, psi0, 3)
+    ref = oracle.step(op, psi0, 0, 3)
+    e = rel_l2(psi, ref)
+    print("rel L2", e)
+    assert e < TOL_PSI[fp64]
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_observables_parity(fp64, dim):
+    if dim == 3:
+        n, h, nu = (32, 32, 64), (0.3, 0.3, 0.2), (1.0, 1.2, 2.0)
+    else:
+        n, h, nu = (64, 64), (0.2, 0.2), (1.0, 1.5)
+    op, kc, psi0 = make_case(dim, n, h, nu, 60.0, 30.0, 1e-3, False, noise=0.05)
+    with dgpe.Solver(dim, n, h, nu, 60.0, 30.0, 1e-3, False, fp64) as s:
+        s.set_psi(psi0)
+        o = s.observables()
+    r = oracle.observables(op, psi0)
+    tol = TOL_MU[fp64]
+    for k in ("norm", "mu", "energy", "kin", "pot", "contact", "rms_r"):
+        assert abs(o[k] - r[k]) <= tol * max(1.0, abs(r[k])), (k, o[k], r[k])
+    assert abs(o["dipolar"] - r["dipolar"]) <= tol * max(1.0, abs(r["mu"]))
+    for a in range(dim):
+        assert abs(o["rms"][a] - r["rms"][a]) <= tol * r["rms"][a]
+
+
+def test_imag3d_config_full_length():
+    """32^3, h = 0.25, V = (x^2 + y^2 + 4 z^2)/2, g = 50, g_dd = 15,
+    imaginary dt = 0.002, 500 steps from the noisy Gaussian, both forms."""
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=50, gdd=15, dt=0.002, imag=True, kernel="dipolar3d")
+    psi0 = synth.gaussian_state(n, h, (1.0, 1.0, 2.0), 0.01, 1601)
+    ref = oracle.step(op, psi0, 0, 500)
+    r = oracle.observables(op, ref, 500)
+    for fp64 in (True, False):
+        psi, o = gpu_run(3, n, h, nu, 50, 15, 0.002, True, fp64, None, psi0, 500)
+        e = rel_l2(psi, ref)
+        print("fp64" if fp64 else "fp32", "rel L2", e, "mu", o["mu"], r["mu"])
+        assert e < TOL_PSI[fp64]
+        assert abs(o["mu"] - r["mu"]) <= TOL_MU[fp64] * abs(r["mu"])
+        assert abs(o["energy"] - r["energy"]) <= TOL_MU[fp64] * abs(r["energy"])
+
+
+def test_real3d_256_short_parity():
+    """256^3 real-time workload (h = 0.1, cigar trap, g = 150 after the quench,
+    g_dd = 60, dt = 5e-4) from a Gaussian stand-in for the ground state:
+    three steps against the oracle, both forms."""
+    n, h, nu = (256, 256, 256), (0.1,) * 3, (1.0, 1.0, 0.5)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=150, gdd=60, dt=5e-4, imag=False, kernel="dipolar3d")
+    psi0 = synth.gaussian_state(n, h, (0.6, 0.6, 0.3), 0.01, 2000)
+    ref = oracle.step(op, psi0, 0, 3)
+    for fp64 in (True, False):
+        psi, o = gpu_run(3, n, h, nu, 150, 60, 5e-4, False, fp64, None, psi0, 3)
+        e = rel_l2(psi, ref)
+        print("fp64" if fp64 else "fp32", "rel L2", e)
+        assert e < TOL_PSI[fp64]
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_real_time_norm_conserved(fp64):
+    n, h, nu = (64, 64, 64), (0.2,) * 3, (1.0, 1.0, 0.5)
+    psi0 = synth.gaussian_state(n, h, (1.0, 1.0, 0.5), 0.01, 7)
+    with dgpe.Solver(3, n, h, nu, 150, 60, 5e-4, False, fp64) as s:
+        s.set_psi(psi0)
+        n0 = s.observables()["norm"]
+        s.step(2000)
+        n1 = s.observables()["norm"]
+    print("norm drift", n1 / n0 - 1)
+    assert abs(n1 / n0 - 1) < (1e-12 if fp64 else 1e-5)
+
+
+def test_fp32_bulk_full_length_64():
+    """2000 real-time steps at 64^3 against the oracle: the FP32-bulk bound."""
+    n, h, nu = (64, 64, 64), (0.2,) * 3, (1.0, 1.0, 0.5)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=150, gdd=60, dt=5e-4, imag=False, kernel="dipolar3d")
+    psi0 = synth.gaussian_state(n, h, (0.8, 0.8, 0.4), 0.01, 9)
+    ref = oracle.step(op, psi0, 0, 2000)
+    psi, o = gpu_run(3, n, h, nu, 150, 60, 5e-4, False, False, None, psi0, 2000)
+    e = rel_l2(psi, ref)
+    r = oracle.observables(op, ref, 2000)
+    print("fp32 2000 steps rel L2", e, "mu", o["mu"], r["mu"])
+    assert e < TOL_PSI[False]
+    assert abs(o["mu"] - r["mu"]) <= TOL_MU[False] * abs(r["mu"])
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_graph_and_direct_launch_identical(fp64):
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    op, kc, psi0 = make_case(3, n, h, nu, 50.0, 15.0, 2e-3, True)
+    a, _ = gpu_run(3, n, h, nu, 50.0, 15.0, 2e-3, True, fp64, kc, psi0, 5, graph=True)
+    b, _ = gpu_run(3, n, h, nu, 50.0, 15.0, 2e-3, True, fp64, kc, psi0, 5, graph=False)
+    assert np.array_equal(a, b)
+
+
+def test_quench_mode_switch_modulation_time():
+    """set_g, set_mode, a trap modulation and the step counter against the
+    oracle's V(t) = V0 (1 + sum_m c_m sin(m t_n)), t_n = n dt."""
+    n, h, nu = (32, 32, 32), (0.3,) * 3, (1.0, 1.0, 1.5)
+    cm = list(synth.trap_modulation(160104640, 8, 0.05))
+    psi0 = synth.gaussian_state(n, h, nu, 0.01, 4)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=60, gdd=20, dt=0.01, imag=True, kernel="dipolar3d")
+    ref = oracle.step(op, psi0, 0, 5)
+    op.imag = False
+    op.g = 45.0
+    op.cm = cm
+    ref = oracle.step(op, ref, 5, 7)
+    with dgpe.Solver(3, n, h, nu, 60, 20, 0.01, True, True) as s:
+        s.set_psi(psi0)
+        s.step(5)
+        s.set_mode(False)
+        s.set_g(45.0)
+        s.set_trap_modulation(cm)
+        assert s.time() == 5
+        s.step(7)
+        assert s.time() == 12
+        psi = s.get_psi()
+        o = s.observables()
+    e = rel_l2(psi, ref)
+    print("rel L2", e)
+    assert e < TOL_PSI[True]
+    r = oracle.observables(op, ref, 12)
+    assert abs(o["mu"] - r["mu"]) <= 1e-11 * abs(r["mu"])
+    assert abs(o["t"] - 0.12) < 1e-15
+
+
+def test_nonfinite_state_reported():
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    psi0 = synth.gaussian_state(n, h, nu, 0.0)
+    psi0[3, 4, 5] = np.nan
+    with dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, True, True) as s:
+        s.set_psi(psi0)
+        with pytest.raises(dgpe.DgpeError) as e:
+            s.observables()
+        assert e.value.code == dgpe.DGPE_ENONFINITE
+
+
+def test_device_pointer_roundtrip():
+    torch = pytest.importorskip("torch")
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    psi0 = synth.gaussian_state(n, h, nu, 0.01, 5)
+    for fp64 in (True, False):
+        with dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, False, fp64) as s:
+            t = torch.from_numpy(psi0).to("cuda")
+            dgpe.dgpe_set_psi_device(s.h, t.data_ptr(), t.numel(), True)
+            out = torch.empty_like(t)
+            dgpe.dgpe_get_psi_device(s.h, out.data_ptr(), out.numel(), True)
+            s.sync()
+            assert np.max(np.abs(out.cpu().numpy() - psi0)) <= (0 if fp64 else 1e-7)
+            host = s.get_psi()
+            assert np.array_equal(host, out.cpu().numpy())
