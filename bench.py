@@ -1,0 +1,321 @@
+"""Benchmark: 3D split-step site-updates/s of the dipolar GP solver (FP64 and
+FP32-bulk forms) and the fraction of the HBM roofline of the dominant kernel.
+
+Workload (default): real-time 256^3 grid, spacing 0.1, cigar trap
+V = (x^2 + y^2 + 0.25 z^2)/2, g_dd = 60, dt = 5e-4; the state is an
+imaginary-time ground state at g = 200 (prepared on the GPU, untimed) and g is
+quenched to 150 before the timed steps.  One step = one full split step over
+the grid (all passes).  Inputs are synthetic (seeded Gaussian + 1% noise).
+
+`python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]`
+prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica (the single-grid step does not shard); value = all ranks' site updates
+/ the slowest rank's time.  `--impl reference` times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "real3d": dict(n=(256, 256, 256), h=(0.1, 0.1, 0.1), nu=(1.0, 1.0, 0.5), g_prep=200.0, g=150.0,
+                   gdd=60.0, dt=5e-4, widths=(1.0, 1.0, 0.5), seed=2016, prep_steps=400,
+                   desc="real3d 256^3, h=0.1, cigar nu=(1,1,0.5), g 200->150 quench, g_dd=60, dt=5e-4, "
+                        "real time from the imaginary-time ground state"),
+    "large": dict(n=(512, 512, 256), h=(0.08, 0.08, 0.08), nu=(1.0, 1.0, 3.0), g_prep=None, g=500.0,
+                  gdd=200.0, dt=2e-4, widths=(1.0, 1.0, 3.0), seed=2016, prep_steps=0,
+                  desc="large real3d 512x512x256, h=0.08, pancake nu=(1,1,3), g=500, g_dd=200, "
+                       "dt=2e-4, from a seeded Gaussian"),
+    "imag3d": dict(n=(32, 32, 32), h=(0.25, 0.25, 0.25), nu=(1.0, 1.0, 2.0), g_prep=None, g=50.0,
+                   gdd=15.0, dt=2e-3, widths=(1.0, 1.0, 2.0), seed=1601, prep_steps=0, imag=True,
+                   desc="imag3d 32^3, h=0.25, nu=(1,1,2), g=50, g_dd=15, imaginary dt=0.002"),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1601_04640_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, form, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get("%s/%s/%s" % (workload, form, kernel))
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_sample(wl, seconds=12.0, max_steps=3):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_1601_04640_gb300 import synth
+    n = wl["n"]
+    p = oracle.Params(dim=3, n=n, h=wl["h"], nu=wl["nu"], g=wl["g"], gdd=wl["gdd"], dt=wl["dt"],
+                      imag=wl.get("imag", False), kernel="dipolar3d")
+    psi = synth.gaussian_state(n, wl["h"], wl["widths"], 0.01, wl["seed"])
+    sites = n[0] * n[1] * n[2]
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        psi = oracle.step(p, psi, steps, 1)
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sites * steps / dt, "unit": "site-updates/s", "cores": oracle.threads(),
+            "kind": "oracle", "sample": "%d full step(s) of the %dx%dx%d workload, FP64 C oracle" % (
+                steps, n[0], n[1], n[2])}, steps, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="real3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--prep-steps", type=int, default=None,
+                    help="imaginary-time preparation steps (default: the workload's)")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.prep_steps is not None:
+        wl["prep_steps"] = args.prep_steps
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n = wl["n"]
+    sites = n[0] * n[1] * n[2]
+    metric = "3D split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle.build
+        oracle.build.build()
+        W = max(0, min(args.warmup, 1))
+        if W:
+            run_oracle_sample(wl, seconds=0.0, max_steps=1)
+        cb, steps, dt = run_oracle_sample(wl, seconds=1e9, max_steps=max(1, args.steps))
+        line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": "site-updates/s",
+                "n_gpus": 0, "steps": steps, "warmup": W, "ms_per_step": 1e3 * dt / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": wl["desc"], "grid": list(n)},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_1601_04640_gb300 import build as gbuild
+    from paper_1601_04640_gb300 import dgpe, synth
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    gbuild.build()
+    dgpe.load()
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+    imag = wl.get("imag", False)
+
+    # ground state (imaginary time at g_prep), prepared once in FP32-bulk
+    psi0 = synth.gaussian_state(n, wl["h"], wl["widths"], 0.01, wl["seed"])
+    prep = None
+    if wl["g_prep"] is not None and wl["prep_steps"] > 0:
+        with dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g_prep"], wl["gdd"], 2e-3, True, False,
+                         stream=stream.cuda_stream) as s:
+            s.set_psi(psi0)
+            s.step(wl["prep_steps"])
+            prep = s.observables()
+            psi0 = s.get_psi()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    forms = {}
+    for fp64 in (True, False):
+        name = "fp64" if fp64 else "fp32_bulk"
+        S = dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64,
+                        stream=stream.cuda_stream)
+        S.set_psi(psi0)
+        S.step(args.warmup)
+        barrier()
+        clk = Clocks(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.step(args.steps)
+        e1.record(stream)
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+        obs = S.observables()
+        # per-pass durations (passes launched one by one, events between them)
+        passes = dgpe.dgpe_profile_steps(S.h, max(3, args.steps // 2))
+        launches = dgpe.dgpe_launches_per_step(S.h) * args.steps
+        tot = sum(p[1] for p in passes)
+        top = max(passes, key=lambda p: p[1])
+        achieved = top[2] / (top[1] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": top[0], "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": ncu_traffic(top[0], name, args.workload),
+                "algorithmic_bytes_per_launch": top[2], "ms_per_launch": top[1]}
+        step_bytes = sum(p[2] for p in passes)
+        f = {"value": world * sites * args.steps / (ms_max * 1e-3), "ms_per_step": ms_max / args.steps,
+             "dtype": "f64" if fp64 else "f32 (FP64 reductions/tables)", "roofline": roof,
+             "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
+                          "achieved_GBps": step_bytes / (ms_max / args.steps * 1e-3) / 1e9,
+                          "frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / hbm_peak},
+             "passes": [{"kernel": p[0], "ms": p[1], "share": p[1] / tot, "GBps": p[2] / (p[1] * 1e-3) / 1e9}
+                        for p in passes],
+             "gpu_launches": launches, "clocks": clocks,
+             "observables_after": {"norm": obs["norm"], "mu": obs["mu"], "energy": obs["energy"]}}
+        # end to end through the C ABI with host buffers: every step copies
+        # the state in from pinned host memory and reads it back
+        if not args.no_e2e:
+            host_in = torch.from_numpy(psi0.view(np.float64).copy()).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            lib = dgpe.load()
+            ke = max(2, min(args.steps, 10))
+            for _ in range(2):
+                dgpe._check(lib.dgpe_set_psi(S.h, host_in.data_ptr(), sites), S.h)
+                S.step(1)
+                dgpe._check(lib.dgpe_get_psi(S.h, host_out.data_ptr(), sites), S.h)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                dgpe._check(lib.dgpe_set_psi(S.h, host_in.data_ptr(), sites), S.h)
+                S.step(1)
+                dgpe._check(lib.dgpe_get_psi(S.h, host_out.data_ptr(), sites), S.h)
+            barrier()
+            te = time.perf_counter() - t0
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            if world > 1:
+                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            f["e2e"] = {"value": world * sites * ke / float(tt.item()), "unit": "site-updates/s",
+                        "h2d_bytes_per_step": 16 * sites, "d2h_bytes_per_step": 16 * sites,
+                        "steps": ke}
+        S.close()
+        forms[name] = f
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle.build
+        oracle.build.build()
+        cpu, _, _ = run_oracle_sample(wl)
+    a = forms["fp64"]
+    b = forms["fp32_bulk"]
+    line = {
+        "metric": metric, "value": a["value"], "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": a["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "grid": list(n), "sites": sites, "form": "fp64",
+                   "l2": "inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
+                       16 * sites >> 20, 8 * sites >> 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
+                                                      "mu": prep["mu"]}},
+        "roofline": a["roofline"], "step_hbm": a["step_hbm"], "passes": a["passes"],
+        "cpu_baseline": cpu, "e2e": a.get("e2e"), "gpu_launches": a["gpu_launches"] + b["gpu_launches"],
+        "clocks": a["clocks"], "observables_after": a["observables_after"],
+        "fp32_bulk": b,
+        "speedup_fp32_bulk_vs_fp64": b["value"] / a["value"],
+        "source_hash": source_hash(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

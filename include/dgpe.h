@@ -151,6 +151,17 @@ int dgpe_sync(dgpe_t h);
 /* Number of kernel launches one dgpe_step(1) makes. */
 int dgpe_launches_per_step(dgpe_t h);
 
+/* Profiling: run n steps with the passes launched one by one on the stream
+ * and a CUDA event recorded between consecutive passes; pass_ms[i] receives
+ * the mean duration (ms) of pass i over the n steps.  Returns the number of
+ * passes of one step (<= cap) or a negative status.  Synchronises. */
+int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap);
+
+/* Kernel name of pass i of one step, and its algorithmic HBM traffic per
+ * launch in bytes (each array element the pass must read or write, once). */
+const char *dgpe_pass_name(dgpe_t h, int i);
+double dgpe_pass_bytes(dgpe_t h, int i);
+
 /* Text of the last error of h (or of the last failed dgpe_create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *dgpe_last_error(dgpe_t h);

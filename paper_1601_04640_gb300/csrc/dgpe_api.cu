@@ -175,3 +175,15 @@ extern "C" int dgpe_launches_per_step(dgpe_t h) {
 extern "C" const char *dgpe_last_error(dgpe_t h) {
   return h ? h->err.c_str() : g_create_err.c_str();
 }
+
+extern "C" int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap) {
+  CHECK_H(h);
+  if (n < 0 || !pass_ms) return fail(h, DGPE_EINVAL, "bad arguments");
+  int rc = h->eng->profile_steps(n, pass_ms, cap, h->stream);
+  if (rc < 0) h->err = h->eng->err;
+  return rc;
+}
+
+extern "C" const char *dgpe_pass_name(dgpe_t h, int i) { return h ? h->eng->pass_name(i) : ""; }
+
+extern "C" double dgpe_pass_bytes(dgpe_t h, int i) { return h ? h->eng->pass_bytes(i) : 0.0; }

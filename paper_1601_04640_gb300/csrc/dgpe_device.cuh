@@ -196,50 +196,68 @@ template <int RAD, bool INV, typename C> __device__ __forceinline__ void dft(C *
 // ------------------------------------------------- Stockham FFT over a tile
 // Radix sequence of one line length (forward order; the inverse runs it
 // reversed so that its first stage reads what the forward's last wrote).
+// Every length and radix product here is a power of two, so index arithmetic
+// uses shifts and masks.
 struct FftPlan {
   int n;
   int ns;
   int rad[10];
 };
 
-// One Stockham stage with radix RAD over `nlines` lines of length n held in
-// shared memory at sm[l*SL + a*SA].  Butterfly j of a line reads elements
-// j + r n/RAD, twiddles them by w_{Ns RAD}^{(j mod Ns) r}, applies the RAD-point
-// DFT and writes element (j / Ns) Ns RAD + (j mod Ns) + r Ns.  The first stage
-// reads through `load` instead of shared memory and the last writes through
-// `store` (its outputs are in natural order).  Each thread owns EPT / RAD
-// butterflies, so all of its values stay in registers across the barrier
-// that separates the reads from the writes (in-place update).
-template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, class Load, class Store>
-__device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines, int n, int Ns,
+template <int V> struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
+template <> struct Log2<1> { static constexpr int value = 0; };
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// Shared-memory index of element a of line l.  Line-major tiles (SA = 1) pad
+// one element after every PADW elements (PADW elements = 128 bytes), which
+// makes every Stockham read and write pattern conflict-free; column tiles
+// (SL = 1) need no pad.
+template <int PADW> __device__ __forceinline__ int sidx(int l, int a, int SL, int SA) {
+  if (PADW > 0) return l * SL + a + (a / PADW);
+  return l * SL + a * SA;
+}
+
+// One Stockham stage with radix RAD over `nlines` lines of length n (2^ln)
+// held in shared memory.  Butterfly j of a line reads elements j + r n/RAD,
+// twiddles them by w_{Ns RAD}^{(j mod Ns) r}, applies the RAD-point DFT and
+// writes element (j / Ns) Ns RAD + (j mod Ns) + r Ns.  The first stage reads
+// through `load` instead of shared memory and the last writes through `store`
+// (its outputs are in natural order).  Each thread owns EPT / RAD butterflies,
+// so all of its values stay in registers across the barrier that separates
+// the reads from the writes (in-place update).
+template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, class Load, class Store>
+__device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines, int ln, int lNs,
                                           bool first, bool last, const cx<R> *__restrict__ tw,
                                           Load &load, Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
+  constexpr int LR = Log2<RAD>::value;
   const int T = blockDim.x, t = threadIdx.x;
-  const int nbl = n / RAD;
+  const int lnbl = ln - LR, nbl = 1 << lnbl;
   const int B = nbl * nlines;
-  const int tstride = n / (Ns * RAD);
+  const int lnl = LINE_FAST ? ilog2(nlines) : 0;
+  const int Ns = 1 << lNs;
+  const int tshift = ln - lNs - LR;  // twiddle stride n / (Ns RAD)
   cx<R> v[EPT];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     const bool ok = b < B;
-    const int l = LINE_FAST ? (b % nlines) : (b / nbl);
-    const int j = LINE_FAST ? (b / nlines) : (b % nbl);
+    const int l = LINE_FAST ? (b & (nlines - 1)) : (b >> lnbl);
+    const int j = LINE_FAST ? (b >> lnl) : (b & (nbl - 1));
     cx<R> *u = v + i * RAD;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-      const int a = j + r * nbl;
+      const int a = j + (r << lnbl);
       if (!ok) u[r] = czero<cx<R>>();
       else if (first) u[r] = load(l, a);
-      else u[r] = sm[l * SL + a * SA];
+      else u[r] = sm[sidx<PADW>(l, a, SL, SA)];
     }
     if (!first) {
-      const int k = j % Ns;
+      const int k = j & (Ns - 1);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        cx<R> w = tw[k * r * tstride];
+        cx<R> w = tw[(k * r) << tshift];
         u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
       }
     }
@@ -250,15 +268,15 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines,
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     if (b < B) {
-      const int l = LINE_FAST ? (b % nlines) : (b / nbl);
-      const int j = LINE_FAST ? (b / nlines) : (b % nbl);
-      const int base = (j / Ns) * Ns * RAD + (j % Ns);
+      const int l = LINE_FAST ? (b & (nlines - 1)) : (b >> lnbl);
+      const int j = LINE_FAST ? (b >> lnl) : (b & (nbl - 1));
+      const int base = ((j >> lNs) << (lNs + LR)) + (j & (Ns - 1));
       cx<R> *u = v + i * RAD;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
-        const int a = base + r * Ns;
+        const int a = base + (r << lNs);
         if (last) store(l, a, u[r]);
-        else sm[l * SL + a * SA] = u[r];
+        else sm[sidx<PADW>(l, a, SL, SA)] = u[r];
       }
     }
   }
@@ -266,23 +284,21 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines,
 }
 
 // Full transform of every line of the tile.  tw[t] = exp(-2 pi i t / n).
-template <typename R, int EPT, bool INV, bool LINE_FAST, class Load, class Store>
+template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, class Load, class Store>
 __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
                          const cx<R> *__restrict__ tw, Load load, Store store) {
-  int Ns = 1;
+  const int ln = ilog2(pl.n);
+  int lNs = 0;
   for (int s = 0; s < pl.ns; ++s) {
     const int rad = INV ? pl.rad[pl.ns - 1 - s] : pl.rad[s];
     const bool first = (s == 0), last = (s == pl.ns - 1);
     switch (rad) {
-      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
-      case 3: if constexpr (EPT % 3 == 0) fft_stage<R, EPT, 3, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
-      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
-      case 5: if constexpr (EPT % 5 == 0) fft_stage<R, EPT, 5, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
-      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
-      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST>(sm, SL, SA, nlines, pl.n, Ns, first, last, tw, load, store); break;
+      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 1; break;
+      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 2; break;
+      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 3; break;
+      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 4; break;
       default: break;
     }
-    Ns *= rad;
   }
 }
 
@@ -293,41 +309,50 @@ __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &p
 // LU of A: m_0 = 1/(1+2kt), m_a = 1/(1+2kt - kt^2 m_{a-1}), alpha_a = kt m_a;
 //   forward  y_a = alpha_a y_{a-1} + m_a r_a,
 //   backward w_a = y_a + alpha_a w_{a+1}.
-// Both first-order recurrences are split into TPL chunks of C points (one per
-// lane of a TPL-wide lane segment); chunk-local passes with zero inflow, a
-// Kogge-Stone scan of the chunk maps (P, Y) -> over the lanes, and a fix-up
+// Both first-order recurrences are split into TPL chunks of CL points (one
+// per lane of a TPL-wide lane segment); chunk-local passes with zero inflow,
+// a Kogge-Stone scan of the chunk maps (P, Y) over the lanes, and a fix-up
 // with the in-chunk products P_a = prod_{b=a0..a} alpha_b and
-// Q_a = prod_{b=a..a0+C-1} alpha_b.  tab holds m, alpha, P, Q (n each).
-// The line lives in shared memory at line[a + a / C] (one pad per chunk keeps
-// the lane accesses on distinct banks).
-template <typename R, typename Coef, int CMAX>
-__device__ __forceinline__ void cn_line(cx<R> *line, int n, int C, int TPL, int q, Coef kt,
+// Q_a = prod_{b=a..a0+CL-1} alpha_b.  With TABLES the kernel reads m, alpha,
+// P, Q (n each, in that order); without, it reads m and forms alpha, P, Q in
+// registers (cheaper where arithmetic is plentiful).  The line lives in shared
+// memory at line[a + a / CL] (one pad per chunk keeps the lanes' accesses on
+// distinct banks).
+template <typename R, typename Coef, int CL, bool TABLES>
+__device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef kt,
                                         const Coef *__restrict__ tab, bool active) {
   typedef cx<R> Cx;
   const Coef *tm = tab, *ta = tab + n, *tp = tab + 2 * n, *tq = tab + 3 * n;
-  const int a0 = q * C;
-  Cx y[CMAX];
-  // right-hand side and chunk-local forward recurrence
+  const int a0 = q * CL;
+  Cx y[CL];
+  Coef mm[CL];  // m_a of the chunk (the on-the-fly path forms alpha, P, Q from it)
   Cx acc = czero<Cx>();
-  Cx prev = (active && a0 > 0) ? line[(a0 - 1) + (a0 - 1) / C] : czero<Cx>();
-  Cx cur = active ? line[a0 + a0 / C] : czero<Cx>();
+  Cx prev = (active && a0 > 0) ? line[(a0 - 1) + (a0 - 1) / CL] : czero<Cx>();
+  Cx cur = active ? line[a0 + a0 / CL] : czero<Cx>();
   const Coef m2kt = coef_scale(kt, (R)(-2));
+  Coef P = coef_one<Coef>();
 #pragma unroll
-  for (int i = 0; i < CMAX; ++i) {
-    if (i < C) {
-      const int a = a0 + i;
-      Cx nxt = (active && a + 1 < n) ? line[(a + 1) + (a + 1) / C] : czero<Cx>();
-      Cx lap = cur + cur - prev - nxt;
-      Cx r = coef_mul(m2kt, lap);
-      Coef ma = active ? tm[a] : coef_zero<Coef>(), al = active ? ta[a] : coef_zero<Coef>();
-      acc = coef_mul(al, acc) + coef_mul(ma, r);
-      y[i] = acc;
-      prev = cur;
-      cur = nxt;
+  for (int i = 0; i < CL; ++i) {
+    const int a = a0 + i;
+    Cx nxt = (active && a + 1 < n) ? line[(a + 1) + (a + 1) / CL] : czero<Cx>();
+    Cx lap = cur + cur - prev - nxt;
+    Cx r = coef_mul(m2kt, lap);
+    const Coef ma = active ? tm[a] : coef_zero<Coef>();
+    Coef al;
+    if (TABLES) {
+      al = active ? ta[a] : coef_zero<Coef>();
+    } else {
+      mm[i] = ma;
+      al = coef_prod(kt, ma);
+      P = coef_prod(P, al);
     }
+    acc = coef_mul(al, acc) + coef_mul(ma, r);
+    y[i] = acc;
+    prev = cur;
+    cur = nxt;
   }
   // inclusive scan over the chunks (lane segment of width TPL)
-  Coef P = active ? tp[a0 + C - 1] : coef_zero<Coef>();
+  if (TABLES) P = active ? tp[a0 + CL - 1] : coef_zero<Coef>();
   Cx Y = acc;
   for (int d = 1; d < TPL; d <<= 1) {
     Coef Pn = shfl_up(P, d, TPL);
@@ -336,21 +361,26 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int C, int TPL, int 
   }
   Cx yin = shfl_up(Y, 1, TPL);
   if (q == 0) yin = czero<Cx>();
+  Coef run = coef_one<Coef>();
 #pragma unroll
-  for (int i = 0; i < CMAX; ++i)
-    if (i < C) y[i] = y[i] + coef_mul(active ? tp[a0 + i] : coef_zero<Coef>(), yin);
+  for (int i = 0; i < CL; ++i) {
+    Coef f;
+    if (TABLES) f = active ? tp[a0 + i] : coef_zero<Coef>();
+    else { run = coef_prod(run, coef_prod(kt, mm[i])); f = run; }
+    y[i] = y[i] + coef_mul(f, yin);
+  }
   // chunk-local backward recurrence
   acc = czero<Cx>();
+  Coef Q = coef_one<Coef>();
 #pragma unroll
-  for (int i = CMAX - 1; i >= 0; --i) {
-    if (i < C) {
-      const int a = a0 + i;
-      Coef al = active ? ta[a] : coef_zero<Coef>();
-      acc = y[i] + coef_mul(al, acc);
-      y[i] = acc;
-    }
+  for (int i = CL - 1; i >= 0; --i) {
+    Coef al;
+    if (TABLES) al = active ? ta[a0 + i] : coef_zero<Coef>();
+    else { al = coef_prod(kt, mm[i]); Q = coef_prod(Q, al); }
+    acc = y[i] + coef_mul(al, acc);
+    y[i] = acc;
   }
-  Coef Q = active ? tq[a0] : coef_zero<Coef>();
+  if (TABLES) Q = active ? tq[a0] : coef_zero<Coef>();
   Cx W = acc;
   for (int d = 1; d < TPL; d <<= 1) {
     Coef Qn = shfl_down(Q, d, TPL);
@@ -359,15 +389,18 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int C, int TPL, int 
   }
   Cx win = shfl_down(W, 1, TPL);
   if (q == TPL - 1) win = czero<Cx>();
+  run = coef_one<Coef>();
   if (active) {
 #pragma unroll
-    for (int i = 0; i < CMAX; ++i)
-      if (i < C) {
-        const int a = a0 + i;
-        Cx w = y[i] + coef_mul(tq[a], win);
-        const int ia = a + a / C;
-        line[ia] = line[ia] + w;
-      }
+    for (int i = CL - 1; i >= 0; --i) {
+      const int a = a0 + i;
+      Coef f;
+      if (TABLES) f = tq[a];
+      else { run = coef_prod(run, coef_prod(kt, mm[i])); f = run; }
+      Cx w = y[i] + coef_mul(f, win);
+      const int ia = a + a / CL;
+      line[ia] = line[ia] + w;
+    }
   }
 }
 

@@ -34,6 +34,9 @@ struct Engine {
   virtual int set_time(long long step, cudaStream_t s) = 0;
   virtual int get_time(long long *step, cudaStream_t s) = 0;
   virtual int launches_per_step() const = 0;
+  virtual int profile_steps(int n, double *pass_ms, int cap, cudaStream_t s) = 0;
+  virtual const char *pass_name(int i) const = 0;
+  virtual double pass_bytes(int i) const = 0;
   virtual size_t sites() const = 0;
   std::string err;
 };
@@ -90,7 +93,8 @@ template <typename R> struct EngineT : Engine {
   typedef cx<R> Cx;
   static constexpr int EPT_X = 8;                  // x-pass elements per thread
   static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFT passes
-  static constexpr int CMAX = 16;                  // CN chunk length bound
+  static constexpr int CMAX = 16;                  // CN chunk length (every axis)
+  static constexpr int PW = 128 / (int)sizeof(Cx); // pad period of line-major tiles
   static constexpr int W = 128 / (int)sizeof(Cx);  // columns per strided tile (128 B)
 
   dgpe_params p{};
@@ -116,7 +120,7 @@ template <typename R> struct EngineT : Engine {
   size_t x_smem = 0;
   struct CnCfg { int n, ncols, W, TPL, C, pitch, T; long long es, os; dim3 grid; size_t smem; };
   CnCfg cn[3];   // index = axis (0 unused: x is fused into P1)
-  struct FtCfg { int n, T; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
+  struct FtCfg { int n, T, W; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
   FtCfg fy{}, fz{};
   int obs_rows = 1, obs_blocks = 0, ndip = 0;
 
@@ -222,11 +226,11 @@ template <typename R> struct EngineT : Engine {
     if (nx % x_C) { err = "nx must be a multiple of 16"; return DGPE_EUNSUPPORTED; }
     x_TPL = nx / x_C;
     if (x_TPL > 32) { err = "nx > 512 not supported"; return DGPE_EUNSUPPORTED; }
-    x_LP = std::max(1, 128 / x_TPL);
+    x_LP = std::max(1, (sizeof(R) == 8 ? 64 : DGPE_MAXT / 2) / x_TPL);
     x_T = 2 * x_LP * x_TPL;
-    x_pitchz = nx + 1;
+    x_pitchz = nx + nx / PW + 1;
     x_pitch = nx + nx / x_C + 1;
-    x_smem = sizeof(Cx) * (size_t)std::max(x_LP * x_pitchz, 2 * x_LP * x_pitch);
+    x_smem = sizeof(Cx) * (size_t)(x_LP * x_pitchz + 2 * x_LP * x_pitch);
     {
       const int npairs = (nrows + 1) / 2;
       x_grid = (npairs + x_LP - 1) / x_LP;
@@ -238,17 +242,18 @@ template <typename R> struct EngineT : Engine {
     fz.axis = 2;
     if (has_dip) {
       // y transform over the spectrum
-      fy.n = ny; fy.T = W * ny / EPT_S; fy.es = px; fy.os = (long long)ny * px;
-      fy.grid = dim3((ncol_spec + W - 1) / W, nz); fy.smem = sizeof(Cx) * (size_t)ny * W; fy.pl = ply;
+      // tile width W columns (128 B rows), narrowed so blocks stay <= DGPE_MAXT
+      auto wfor = [&](int n) { return std::max(1, std::min(W, DGPE_MAXT * EPT_S / n)); };
+      fy.n = ny; fy.W = wfor(ny); fy.T = fy.W * ny / EPT_S; fy.es = px; fy.os = (long long)ny * px;
+      fy.grid = dim3((ncol_spec + fy.W - 1) / fy.W, nz); fy.smem = sizeof(Cx) * (size_t)ny * fy.W; fy.pl = ply;
       if (dim == 3) {
-        fz.n = nz; fz.T = W * nz / EPT_S; fz.es = (long long)ny * px; fz.os = px;
-        fz.grid = dim3((ncol_spec + W - 1) / W, ny); fz.smem = sizeof(Cx) * (size_t)nz * W; fz.pl = plz;
+        fz.n = nz; fz.W = wfor(nz); fz.T = fz.W * nz / EPT_S; fz.es = (long long)ny * px; fz.os = px;
+        fz.grid = dim3((ncol_spec + fz.W - 1) / fz.W, ny); fz.smem = sizeof(Cx) * (size_t)nz * fz.W; fz.pl = plz;
       }
-      if (fy.T > 1024 || fz.T > 1024) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
+      if (fy.T > DGPE_MAXT || fz.T > DGPE_MAXT) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
     }
     // scratch: norm partials, observable partials
-    obs_rows = std::max(1, (int)(((size_t)nrows + 4095) / 4096));
-    obs_blocks = (nrows + obs_rows - 1) / obs_rows;
+    obs_blocks = (int)std::min<size_t>(152 * 8, (nsites + 255) / 256);
     const FtCfg &last = (dim == 3) ? fz : fy;
     ndip = has_dip ? (int)(last.grid.x * last.grid.y) : 0;
     const CnCfg &fin = cn[dim == 3 ? 2 : 1];
@@ -269,17 +274,16 @@ template <typename R> struct EngineT : Engine {
     const int n = (axis == 1) ? ny : nz;
     c.n = n;
     c.ncols = nx;
-    c.W = W;
-    int tpl = 32;
-    while (tpl > 1 && (n % tpl || n / tpl < 1)) tpl >>= 1;
+    const int tpl = n / CMAX;
+    if (tpl < 1 || tpl > 32 || n % CMAX) { err = "line length not supported by the CN chunking"; return DGPE_EUNSUPPORTED; }
     c.TPL = tpl;
-    c.C = n / tpl;
-    if (c.C > CMAX) { err = "line too long for the CN chunking"; return DGPE_EUNSUPPORTED; }
+    c.C = CMAX;
+    c.W = std::min(W, DGPE_MAXT / tpl);  // blocks of at most DGPE_MAXT threads
     c.pitch = n + n / c.C + 1;
-    c.T = W * tpl;
-    if (axis == 1) { c.es = nx; c.os = (long long)nx * ny; c.grid = dim3((nx + W - 1) / W, nz); }
-    else { c.es = (long long)nx * ny; c.os = nx; c.grid = dim3((nx + W - 1) / W, ny); }
-    c.smem = sizeof(Cx) * (size_t)W * c.pitch;
+    c.T = c.W * tpl;
+    if (axis == 1) { c.es = nx; c.os = (long long)nx * ny; c.grid = dim3((nx + c.W - 1) / c.W, nz); }
+    else { c.es = (long long)nx * ny; c.os = nx; c.grid = dim3((nx + c.W - 1) / c.W, ny); }
+    c.smem = sizeof(Cx) * (size_t)c.W * c.pitch;
     return DGPE_OK;
   }
 
@@ -355,6 +359,7 @@ template <typename R> struct EngineT : Engine {
   template <typename K> int smem_attr(K kernel, size_t bytes) {
     if (bytes > 48 * 1024)
       DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     return DGPE_OK;
   }
   int set_smem_attrs() {
@@ -388,7 +393,7 @@ template <typename R> struct EngineT : Engine {
   SArgs<R> sargs(const FtCfg &f) const {
     SArgs<R> A{};
     A.spec = spec; A.U = U; A.partial = dip_part; A.tw = tw[f.axis]; A.pl = f.pl;
-    A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = W; A.nxh = nx / 2;
+    A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = f.W; A.nxh = nx / 2;
     return A;
   }
   int launch_fft(const FtCfg &f, int mode, cudaStream_t s) {
@@ -444,13 +449,83 @@ template <typename R> struct EngineT : Engine {
     }
     return DGPE_OK;
   }
+  // The passes of one step, in order (id, name, algorithmic HBM bytes).
+  enum { PS_DENS_R2C, PS_FFT_Y, PS_FFT_Z_U, PS_IFFT_Y, PS_FFT_Y_U, PS_P1, PS_CN_Y, PS_CN_Z };
+  std::vector<int> pass_ids() const {
+    std::vector<int> v;
+    if (has_dip) {
+      v.push_back(PS_DENS_R2C);
+      if (dim == 3) { v.push_back(PS_FFT_Y); v.push_back(PS_FFT_Z_U); v.push_back(PS_IFFT_Y); }
+      else v.push_back(PS_FFT_Y_U);
+    }
+    v.push_back(PS_P1);
+    v.push_back(PS_CN_Y);
+    if (dim == 3) v.push_back(PS_CN_Z);
+    return v;
+  }
+  int launch_pass(int id, cudaStream_t s) {
+    switch (id) {
+      case PS_DENS_R2C: return launch_forward_spectrum(s);
+      case PS_FFT_Y: return launch_fft(fy, 0, s);
+      case PS_FFT_Z_U: return launch_fft(fz, 2, s);
+      case PS_IFFT_Y: return launch_fft(fy, 1, s);
+      case PS_FFT_Y_U: return launch_fft(fy, 2, s);
+      case PS_P1: return launch_p1(0, s);
+      case PS_CN_Y: return launch_cn(1, dim == 2, s);
+      default: return launch_cn(2, true, s);
+    }
+  }
   int launch_step(cudaStream_t s) {
-    int rc;
-    if (has_dip && (rc = launch_dipolar_chain(s))) return rc;
-    if ((rc = launch_p1(0, s))) return rc;
-    if ((rc = launch_cn(1, dim == 2, s))) return rc;
-    if (dim == 3 && (rc = launch_cn(2, true, s))) return rc;
+    for (int id : pass_ids()) {
+      int rc = launch_pass(id, s);
+      if (rc) return rc;
+    }
     return DGPE_OK;
+  }
+  const char *pass_name(int i) const override {
+    static const char *names[] = {"dens_r2c_x", "fft_y", "fft_z_u_ifft_z", "ifft_y",
+                                  "fft_y_u_ifft_y", "c2r_x_exp_cn_x", "cn_y", "cn_z"};
+    std::vector<int> v = pass_ids();
+    return (i >= 0 && i < (int)v.size()) ? names[v[i]] : "";
+  }
+  double pass_bytes(int i) const override {
+    std::vector<int> v = pass_ids();
+    if (i < 0 || i >= (int)v.size()) return 0.0;
+    const double S = (double)sizeof(Cx), N = (double)nsites;
+    const double sp = (double)ncol_spec * nrows, ub = sp * sizeof(R);
+    switch (v[i]) {
+      case PS_DENS_R2C: return N * S + sp * S;
+      case PS_FFT_Y: case PS_IFFT_Y: return 2.0 * sp * S;
+      case PS_FFT_Z_U: case PS_FFT_Y_U: return 2.0 * sp * S + ub;
+      case PS_P1: return (has_dip ? sp * S : 0.0) + 2.0 * N * S;
+      default: return 2.0 * N * S;
+    }
+  }
+  int profile_steps(int n, double *pass_ms, int cap, cudaStream_t s) override {
+    std::vector<int> v = pass_ids();
+    const int np = (int)v.size();
+    if (cap < np) { err = "pass_ms too small"; return DGPE_EINVAL; }
+    std::vector<cudaEvent_t> ev(np + 1);
+    for (auto &e : ev) DGPE_CK(cudaEventCreate(&e));
+    std::vector<double> acc(np, 0.0);
+    int rc = DGPE_OK;
+    for (int k = 0; k < n && rc == DGPE_OK; ++k) {
+      for (int i = 0; i < np && rc == DGPE_OK; ++i) {
+        cudaEventRecord(ev[i], s);
+        rc = launch_pass(v[i], s);
+      }
+      cudaEventRecord(ev[np], s);
+      if (cudaEventSynchronize(ev[np]) != cudaSuccess) { err = "event sync failed"; rc = DGPE_ECUDA; }
+      for (int i = 0; i < np && rc == DGPE_OK; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        acc[i] += ms;
+      }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    for (int i = 0; i < np; ++i) pass_ms[i] = n > 0 ? acc[i] / n : 0.0;
+    return np;
   }
   int capture() {
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
@@ -526,7 +601,7 @@ template <typename R> struct EngineT : Engine {
     }
     OArgs<R> A{};
     A.psi = psi; A.prm = prm; A.partial = obs_part; A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
-    A.rows_per_block = obs_rows; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
+    A.rows_per_block = 0; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
     A.nux = p.nu[0]; A.nuy = p.nu[1]; A.nuz = (dim == 3) ? p.nu[2] : 0.0;
     k_obs_sites<R><<<obs_blocks, 256, 0, s>>>(A);
     DGPE_CK(cudaGetLastError());

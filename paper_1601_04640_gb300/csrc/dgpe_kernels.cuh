@@ -83,6 +83,32 @@ template <> __device__ __forceinline__ float make_kt<float>(double tau) { return
 template <> __device__ __forceinline__ double2 make_kt<double2>(double tau) { return make_double2(0.0, tau); }
 template <> __device__ __forceinline__ float2 make_kt<float2>(double tau) { return make_float2(0.0f, (float)tau); }
 
+// sin and cos of a half-angle.  For |x| <= 1/16 the Taylor series of sin and
+// cos truncated after x^11 / x^12 (remainder below 2^-60 relative) replaces
+// the library call; larger arguments use sincos.
+template <typename R> __device__ __forceinline__ void half_sincos(R x, R *s, R *c) {
+  if (fabs((double)x) <= 0.0625) {
+    const R x2 = x * x;
+    // sin x = x (1 - x^2/3! + x^4/5! - x^6/7! + x^8/9! - x^10/11!)
+    R ps = (R)(-1.0 / 39916800.0);
+    ps = ps * x2 + (R)(1.0 / 362880.0);
+    ps = ps * x2 + (R)(-1.0 / 5040.0);
+    ps = ps * x2 + (R)(1.0 / 120.0);
+    ps = ps * x2 + (R)(-1.0 / 6.0);
+    *s = x + x * (x2 * ps);
+    // cos x = 1 - x^2/2! + x^4/4! - x^6/6! + x^8/8! - x^10/10! + x^12/12!
+    R pc = (R)(1.0 / 479001600.0);
+    pc = pc * x2 + (R)(-1.0 / 3628800.0);
+    pc = pc * x2 + (R)(1.0 / 40320.0);
+    pc = pc * x2 + (R)(-1.0 / 720.0);
+    pc = pc * x2 + (R)(1.0 / 24.0);
+    pc = pc * x2 + (R)(-0.5);
+    *c = (R)1 + x2 * pc;
+  } else {
+    fsincos(x, s, c);
+  }
+}
+
 // psi <- psi exp(-kappa theta) in increment form (psi + psi (e - 1)) so that
 // rounding of the factor scales with theta, not with psi.
 template <typename R> __device__ __forceinline__ cx<R> nonlinear_factor(cx<R> v, R th, int imag) {
@@ -91,7 +117,7 @@ template <typename R> __device__ __forceinline__ cx<R> nonlinear_factor(cx<R> v,
     return mk<R>(v.x + v.x * f, v.y + v.y * f);
   }
   R s, c;
-  fsincos(th * (R)0.5, &s, &c);
+  half_sincos<R>(th * (R)0.5, &s, &c);
   const R cm1 = (R)-2 * s * s;   // cos th - 1
   const R sn = (R)2 * s * c;     // sin th
   // v (cm1 - i sn)
@@ -109,10 +135,17 @@ __device__ __forceinline__ double trap_dts(const double *prm, long long step) {
 }
 
 // ------------------------------------------------------------------ P4
+// elements per 128 bytes: the pad period of line-major tiles
+template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx<R>); };
+
+// Every pass is launched with at most DGPE_MAXT threads per block.
+#define DGPE_MAXT 256
+
 template <typename R, int EPT>
-__global__ void k_dens_r2c_x(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
+  constexpr int PW = Pad<R>::W;
   const int n = A.nx, SL = A.pitchz, nrows = A.nrows;
   const int p0 = blockIdx.x * A.LP;
   const R sc = (R)A.prm[PRM_SC];
@@ -125,8 +158,8 @@ __global__ void k_dens_r2c_x(XArgs<R> A) {
     if (r1 < nrows) { cx<R> v = psi[(size_t)r1 * n + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
     return mk<R>(d0, d1);
   };
-  auto store = [&](int l, int a, cx<R> v) { zt[l * SL + a] = v; };
-  tile_fft<R, EPT, false, false>(zt, SL, 1, A.LP, A.pl, A.tw, load, store);
+  auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
+  tile_fft<R, EPT, false, false, PW>(zt, SL, 1, A.LP, A.pl, A.tw, load, store);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
   const int nh = n / 2 + 1;
@@ -134,7 +167,7 @@ __global__ void k_dens_r2c_x(XArgs<R> A) {
     const int l = idx / nh, k = idx - l * nh;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     if (r0 >= nrows) continue;
-    const cx<R> Zk = zt[l * SL + k], Zm = zt[l * SL + (k == 0 ? 0 : n - k)];
+    const cx<R> Zk = zt[sidx<PW>(l, k, SL, 1)], Zm = zt[sidx<PW>(l, (k == 0 ? 0 : n - k), SL, 1)];
     const cx<R> X0 = mk<R>((R)0.5 * (Zk.x + Zm.x), (R)0.5 * (Zk.y - Zm.y));
     const cx<R> X1 = mk<R>((R)0.5 * (Zk.y + Zm.y), (R)0.5 * (Zm.x - Zk.x));
     A.spec[(size_t)r0 * A.px + k] = X0;
@@ -144,30 +177,52 @@ __global__ void k_dens_r2c_x(XArgs<R> A) {
 
 // ------------------------------------------------------------------ P1
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
-template <typename R, typename Coef, int EPT, int CMAX, int MODE>
-__global__ void k_c2r_x_exp_cnx(XArgs<R> A) {
+template <typename R, typename Coef, int EPT, int CL, int MODE>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile, 2 LP lines
-  cx<R> *zt = pt;  // the Z tile aliases it until the last FFT stage's barrier
+  cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
+  cx<R> *zt = pt + 2 * A.LP * A.pitch;           // Z tile: LP lines, pitch pitchz
+  constexpr int PW = Pad<R>::W;
   __shared__ double s_dts;
-  if (threadIdx.x == 0) s_dts = trap_dts(A.prm, *A.step);
-  __syncthreads();
-  const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch, C = A.C;
+  const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
+  const int ln = ilog2(n), lny = ilog2(A.ny);
   const int p0 = blockIdx.x * A.LP;
+  const int T = blockDim.x, t = threadIdx.x;
+  if (MODE == 0) {
+    // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
+    // every load of the tile is issued before any is used (2 LP n = CL T)
+    cx<R> buf[CL];
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      const int L = idx >> ln, a = idx & (n - 1);
+      const int row = 2 * p0 + L;
+      buf[i] = (row < nrows) ? A.psi[(size_t)row * n + a] : czero<cx<R>>();
+    }
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      const int L = idx >> ln, a = idx & (n - 1);
+      pt[L * P + a + a / CL] = buf[i];
+    }
+  }
+  if (t == 0) s_dts = trap_dts(A.prm, *A.step);
+  __syncthreads();
   const R dts = (R)s_dts;
   const R gdt = (R)(A.prm[PRM_DT] * A.prm[PRM_G]);
   const R gdddt = (R)(A.prm[PRM_DT] * A.prm[PRM_GDD]);
   const R sc = (R)A.prm[PRM_SC];
   const int imag = A.imag;
-  const cx<R> *__restrict__ psi = A.psi;
-  auto apply_e = [&](int row, int a, R phi) -> cx<R> {
-    cx<R> v = psi[(size_t)row * n + a];
-    v = cscale(v, sc);
+  // exponential substep on the tile element (L, a) in place
+  auto apply_e = [&](int L, int a, R phi) {
+    const int row = 2 * p0 + L;
+    const int ia = L * P + a + a / CL;
+    cx<R> v = cscale(pt[ia], sc);
     const R dens = v.x * v.x + v.y * v.y;
-    const int y = row % A.ny, z = row / A.ny;
+    const int y = row & (A.ny - 1), z = row >> lny;
     const R V = A.vx[a] + A.vy[y] + A.vz[z];
     const R th = dts * V + gdt * dens + gdddt * phi;
-    return nonlinear_factor<R>(v, th, imag);
+    pt[ia] = nonlinear_factor<R>(v, th, imag);
   };
   if (A.has_dip) {
     auto load = [&](int l, int a) -> cx<R> {
@@ -187,30 +242,27 @@ __global__ void k_c2r_x_exp_cnx(XArgs<R> A) {
         if (r1 < nrows) A.phi_out[(size_t)r1 * n + a] = v.y;
         return;
       }
-      const int ia = a + a / C;
-      pt[(2 * l) * P + ia] = (r0 < nrows) ? apply_e(r0, a, v.x) : czero<cx<R>>();
-      pt[(2 * l + 1) * P + ia] = (r1 < nrows) ? apply_e(r1, a, v.y) : czero<cx<R>>();
+      apply_e(2 * l, a, v.x);
+      apply_e(2 * l + 1, a, v.y);
     };
-    tile_fft<R, EPT, true, false>(zt, A.pitchz, 1, A.LP, A.pl, A.tw, load, store);
-  } else {
-    for (int idx = threadIdx.x; idx < 2 * A.LP * n; idx += blockDim.x) {
-      const int L = idx / n, a = idx - L * n;
-      const int row = 2 * p0 + L;
-      pt[L * P + a + a / C] = (row < nrows) ? apply_e(row, a, (R)0) : czero<cx<R>>();
-    }
+    tile_fft<R, EPT, true, false, PW>(zt, A.pitchz, 1, A.LP, A.pl, A.tw, load, store);
+  } else if (MODE == 0) {
+    for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(idx >> ln, idx & (n - 1), (R)0);
     __syncthreads();
   }
   if (MODE == 1) return;
   // Crank-Nicolson along x: TPL lanes per line
-  const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
+  const int l = t / A.TPL, q = t - l * A.TPL;
   const bool active = (2 * p0 + l) < nrows;
-  cn_line<R, Coef, CMAX>(pt + l * P, n, C, A.TPL, q, make_kt<Coef>(A.tau),
-                         reinterpret_cast<const Coef *>(A.cntab), active);
+  cn_line<R, Coef, CL, (sizeof(R) == 8)>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                                         reinterpret_cast<const Coef *>(A.cntab), active);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 2 * A.LP * n; idx += blockDim.x) {
-    const int L = idx / n, a = idx - L * n;
+#pragma unroll
+  for (int i = 0; i < CL; ++i) {
+    const int idx = t + i * T;
+    const int L = idx >> ln, a = idx & (n - 1);
     const int row = 2 * p0 + L;
-    if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / C];
+    if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
   }
 }
 
@@ -218,7 +270,7 @@ __global__ void k_c2r_x_exp_cnx(XArgs<R> A) {
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
 template <typename R, int EPT, int MODE>
-__global__ void k_fft_strided(SArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
   __shared__ double red[32];
@@ -234,17 +286,17 @@ __global__ void k_fft_strided(SArgs<R> A) {
     if (c0 + l < A.ncols) spec[base + a * es + l] = v;
   };
   if (MODE == 0) {
-    tile_fft<R, EPT, false, true>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
   } else if (MODE == 1) {
-    tile_fft<R, EPT, true, true>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, true, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
   } else if (MODE == 2) {
     auto mstore = [&](int l, int a, cx<R> v) {
       const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
       sm[a * W + l] = cscale(v, u);
     };
-    tile_fft<R, EPT, false, true>(sm, 1, W, W, A.pl, A.tw, gload, mstore);
+    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, mstore);
     auto sload = [&](int l, int a) -> cx<R> { return sm[a * W + l]; };
-    tile_fft<R, EPT, true, true>(sm, 1, W, W, A.pl, A.tw, sload, gstore);
+    tile_fft<R, EPT, true, true, 0>(sm, 1, W, W, A.pl, A.tw, sload, gstore);
   } else {
     double acc = 0.0;
     auto astore = [&](int l, int a, cx<R> v) {
@@ -254,38 +306,51 @@ __global__ void k_fft_strided(SArgs<R> A) {
         acc += w * (double)A.U[base + a * es + l] * ((double)v.x * v.x + (double)v.y * v.y);
       }
     };
-    tile_fft<R, EPT, false, true>(sm, 1, W, W, A.pl, A.tw, gload, astore);
+    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, astore);
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
 
 // ------------------------------------------------------- P2 / P3 (strided)
-template <typename R, typename Coef, int CMAX>
-__global__ void k_cn_strided(CArgs<R> A) {
+template <typename R, typename Coef, int CL>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided(CArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *tile = reinterpret_cast<cx<R> *>(smraw);  // [W][pitch]
   __shared__ double red[32];
   __shared__ int am_last;
-  const int W = A.W, n = A.n, C = A.C, P = A.pitch;
+  const int W = A.W, n = A.n, P = A.pitch;
+  const int lW = ilog2(W);
   const int c0 = blockIdx.x * W;
   const size_t base = (size_t)blockIdx.y * A.ostride + c0;
   const long long es = A.estride;
-  for (int idx = threadIdx.x; idx < n * W; idx += blockDim.x) {
-    const int a = idx / W, l = idx - a * W;
-    tile[l * P + a + a / C] = (c0 + l < A.ncols) ? A.psi[base + a * es + l] : czero<cx<R>>();
+  // thread t owns column t % W and rows t / W + i TPL, i < CL (blockDim =
+  // W TPL, n = CL TPL): all CL loads are in flight before the first
+  // shared-memory store
+  const int lc = threadIdx.x & (W - 1), r0 = threadIdx.x >> lW;
+  {
+    const bool ok = c0 + lc < A.ncols;
+    cx<R> buf[CL];
+#pragma unroll
+    for (int i = 0; i < CL; ++i) buf[i] = ok ? A.psi[base + (size_t)(r0 + i * A.TPL) * es + lc] : czero<cx<R>>();
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int a = r0 + i * A.TPL;
+      tile[lc * P + a + a / CL] = buf[i];
+    }
   }
   __syncthreads();
   const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-  cn_line<R, Coef, CMAX>(tile + l * P, n, C, A.TPL, q, make_kt<Coef>(A.tau),
-                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
+  cn_line<R, Coef, CL, (sizeof(R) == 8)>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
   __syncthreads();
   double acc = 0.0;
-  for (int idx = threadIdx.x; idx < n * W; idx += blockDim.x) {
-    const int a = idx / W, l2 = idx - a * W;
-    if (c0 + l2 < A.ncols) {
-      const cx<R> v = tile[l2 * P + a + a / C];
-      A.psi[base + a * es + l2] = v;
+  if (c0 + lc < A.ncols) {
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int a = r0 + i * A.TPL;
+      const cx<R> v = tile[lc * P + a + a / CL];
+      A.psi[base + (size_t)a * es + lc] = v;
       if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y;
     }
   }
@@ -332,43 +397,39 @@ template <typename R>
 __global__ void k_obs_sites(OArgs<R> A) {
   __shared__ double red[32];
   const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int nrows = ny * nz;
+  const size_t N = (size_t)nx * ny * nz;
   const double sc = A.prm[PRM_SC];
   double acc[OBS_COUNT];
 #pragma unroll
   for (int k = 0; k < OBS_COUNT; ++k) acc[k] = 0.0;
-  const int r_begin = blockIdx.x * A.rows_per_block;
-  const int r_end = min(nrows, r_begin + A.rows_per_block);
   const int nxh = nx / 2, nyh = ny / 2, nzh = nz / 2;
-  for (int r = r_begin; r < r_end; ++r) {
-    const int y = r % ny, z = r / ny;
-    const double Y = (double)(y - nyh) * A.hy, Z = (A.dim == 3) ? (double)(z - nzh) * A.hz : 0.0;
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-      const size_t i = (size_t)r * nx + x;
-      const cx<R> v0 = A.psi[i];
-      const double vr = sc * (double)v0.x, vi = sc * (double)v0.y;
-      const double nn = vr * vr + vi * vi;
-      if (!isfinite(nn)) { acc[OBS_BAD] += 1.0; continue; }
-      const double X = (double)(x - nxh) * A.hx;
-      acc[OBS_N] += nn;
-      acc[OBS_X2] += X * X * nn;
-      acc[OBS_Y2] += Y * Y * nn;
-      acc[OBS_Z2] += Z * Z * nn;
-      acc[OBS_V] += 0.5 * (A.nux * A.nux * X * X + A.nuy * A.nuy * Y * Y + A.nuz * A.nuz * Z * Z) * nn;
-      acc[OBS_N2] += nn * nn;
-      double dr, di;
-      // forward differences with zero ghosts; the (ghost, first) pair adds |psi_0|^2
-      if (x + 1 < nx) { const cx<R> w = A.psi[i + 1]; dr = sc * (double)w.x - vr; di = sc * (double)w.y - vi; }
-      else { dr = -vr; di = -vi; }
-      acc[OBS_KX] += dr * dr + di * di + (x == 0 ? nn : 0.0);
-      if (y + 1 < ny) { const cx<R> w = A.psi[i + nx]; dr = sc * (double)w.x - vr; di = sc * (double)w.y - vi; }
-      else { dr = -vr; di = -vi; }
-      acc[OBS_KY] += dr * dr + di * di + (y == 0 ? nn : 0.0);
-      if (A.dim == 3) {
-        if (z + 1 < nz) { const cx<R> w = A.psi[i + (size_t)nx * ny]; dr = sc * (double)w.x - vr; di = sc * (double)w.y - vi; }
-        else { dr = -vr; di = -vi; }
-        acc[OBS_KZ] += dr * dr + di * di + (z == 0 ? nn : 0.0);
-      }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const size_t r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const cx<R> v0 = A.psi[i];
+    const cx<R> wx = (x + 1 < nx) ? A.psi[i + 1] : czero<cx<R>>();
+    const cx<R> wy = (y + 1 < ny) ? A.psi[i + nx] : czero<cx<R>>();
+    const cx<R> wz = (A.dim == 3 && z + 1 < nz) ? A.psi[i + (size_t)nx * ny] : czero<cx<R>>();
+    const double vr = sc * (double)v0.x, vi = sc * (double)v0.y;
+    const double nn = vr * vr + vi * vi;
+    if (!isfinite(nn)) { acc[OBS_BAD] += 1.0; continue; }
+    const double X = (double)(x - nxh) * A.hx, Y = (double)(y - nyh) * A.hy;
+    const double Z = (A.dim == 3) ? (double)(z - nzh) * A.hz : 0.0;
+    acc[OBS_N] += nn;
+    acc[OBS_X2] += X * X * nn;
+    acc[OBS_Y2] += Y * Y * nn;
+    acc[OBS_Z2] += Z * Z * nn;
+    acc[OBS_V] += 0.5 * (A.nux * A.nux * X * X + A.nuy * A.nuy * Y * Y + A.nuz * A.nuz * Z * Z) * nn;
+    acc[OBS_N2] += nn * nn;
+    // forward differences with zero ghosts; the (ghost, first) pair adds |psi_0|^2
+    double dr = sc * (double)wx.x - vr, di = sc * (double)wx.y - vi;
+    acc[OBS_KX] += dr * dr + di * di + (x == 0 ? nn : 0.0);
+    dr = sc * (double)wy.x - vr; di = sc * (double)wy.y - vi;
+    acc[OBS_KY] += dr * dr + di * di + (y == 0 ? nn : 0.0);
+    if (A.dim == 3) {
+      dr = sc * (double)wz.x - vr; di = sc * (double)wz.y - vi;
+      acc[OBS_KZ] += dr * dr + di * di + (z == 0 ? nn : 0.0);
     }
   }
 #pragma unroll

@@ -39,6 +39,7 @@ EXPORTS = [
     "dgpe_get_psi_device", "dgpe_step", "dgpe_observables", "dgpe_dipolar_potential",
     "dgpe_set_g", "dgpe_set_mode", "dgpe_set_trap_modulation", "dgpe_set_time",
     "dgpe_get_time", "dgpe_sync", "dgpe_launches_per_step", "dgpe_last_error",
+    "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes",
 ]
 
 
@@ -96,6 +97,11 @@ def load(path: str = LIB_PATH):
         lib.dgpe_launches_per_step.argtypes = [H]
         lib.dgpe_last_error.argtypes = [H]
         lib.dgpe_last_error.restype = C.c_char_p
+        lib.dgpe_profile_steps.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.c_int]
+        lib.dgpe_pass_name.argtypes = [H, C.c_int]
+        lib.dgpe_pass_name.restype = C.c_char_p
+        lib.dgpe_pass_bytes.argtypes = [H, C.c_int]
+        lib.dgpe_pass_bytes.restype = C.c_double
         _lib = lib
     return _lib
 
@@ -207,6 +213,16 @@ def dgpe_sync(h):
 
 def dgpe_launches_per_step(h):
     return load().dgpe_launches_per_step(h)
+
+
+def dgpe_profile_steps(h, n):
+    """[(pass name, mean ms per launch, algorithmic bytes per launch)]."""
+    buf = (C.c_double * 16)()
+    rc = load().dgpe_profile_steps(h, int(n), buf, 16)
+    if rc < 0:
+        _check(rc, h)
+    return [(load().dgpe_pass_name(h, i).decode(), buf[i], load().dgpe_pass_bytes(h, i))
+            for i in range(rc)]
 
 
 class Solver:
