@@ -162,6 +162,32 @@ int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap);
 const char *dgpe_pass_name(dgpe_t h, int i);
 double dgpe_pass_bytes(dgpe_t h, int i);
 
+/* Phi_d of |psi|^2 for a caller's state, computed without allocating any
+ * device memory (the paper has no counterpart: this serves callers that must
+ * not call cudaMalloc while they run -- work recorded into another
+ * framework's stream capture, fixed device-memory budgets or caching
+ * allocators that must own every allocation, real-time loops that cannot
+ * afford an allocation's latency or failure).
+ *   psi: device buffer of n_sites complex values, complex128 when fp64 != 0,
+ *        else complex64, layout [z][y][x] / [y][x];
+ *   phi: device buffer of n_sites reals (double when fp64 != 0, else float);
+ *   dim, n, h, kernel, qd: as in dgpe_params (kernel DIPOLAR_3D with dim 3 or
+ *        QUASI2D_XY with dim 2); each n a power of two in [32, 512] and at
+ *        most 262144 sites in total, else DGPE_EUNSUPPORTED;
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ * All scratch (half spectrum, U(k)/N, FFT roots) lives in one 4 MiB static
+ * device array that every GPU loading this library keeps until exit.  The
+ * first call on a device looks up that array's address (with the device
+ * current), so make it before any stream capture.  Every call reuses the same
+ * array and re-initialises what it reads first; calls that overlap on the GPU
+ * (other streams, other threads) race on it.  No allocation of any kind.
+ * Errors: DGPE_EINVAL / DGPE_EUNSUPPORTED / DGPE_ECUDA, text in
+ * dgpe_noalloc_last_error(). */
+int dgpe_dipolar_potential_noalloc(const void *psi, void *phi, int fp64, int dim,
+                                   const int n[3], const double h[3], int kernel,
+                                   double qd, void *cuda_stream);
+const char *dgpe_noalloc_last_error(void);
+
 /* Text of the last error of h (or of the last failed dgpe_create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *dgpe_last_error(dgpe_t h);

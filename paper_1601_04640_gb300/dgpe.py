@@ -40,6 +40,7 @@ EXPORTS = [
     "dgpe_set_g", "dgpe_set_mode", "dgpe_set_trap_modulation", "dgpe_set_time",
     "dgpe_get_time", "dgpe_sync", "dgpe_launches_per_step", "dgpe_last_error",
     "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes",
+    "dgpe_dipolar_potential_noalloc", "dgpe_noalloc_last_error",
 ]
 
 
@@ -102,6 +103,11 @@ def load(path: str = LIB_PATH):
         lib.dgpe_pass_name.restype = C.c_char_p
         lib.dgpe_pass_bytes.argtypes = [H, C.c_int]
         lib.dgpe_pass_bytes.restype = C.c_double
+        lib.dgpe_dipolar_potential_noalloc.argtypes = [
+            C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+            C.c_int, C.c_double, C.c_void_p]
+        lib.dgpe_noalloc_last_error.argtypes = []
+        lib.dgpe_noalloc_last_error.restype = C.c_char_p
         _lib = lib
     return _lib
 
@@ -223,6 +229,21 @@ def dgpe_profile_steps(h, n):
         _check(rc, h)
     return [(load().dgpe_pass_name(h, i).decode(), buf[i], load().dgpe_pass_bytes(h, i))
             for i in range(rc)]
+
+
+def dgpe_dipolar_potential_noalloc(psi_ptr: int, phi_ptr: int, fp64: bool, dim: int, n, h,
+                                   kernel=None, qd=0.5, stream: int = 0):
+    """Phi_d of |psi|^2 from device buffers, with no device allocation (the
+    scratch is a static device array inside libdgpe.so; see include/dgpe.h)."""
+    if kernel is None:
+        kernel = DGPE_KERNEL_DIPOLAR_3D if dim == 3 else DGPE_KERNEL_QUASI2D_XY
+    nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    hh = (C.c_double * 3)(*(list(h) + [1.0] * (3 - len(h))))
+    rc = load().dgpe_dipolar_potential_noalloc(C.c_void_p(psi_ptr), C.c_void_p(phi_ptr),
+                                               1 if fp64 else 0, dim, nn, hh, kernel, float(qd),
+                                               C.c_void_p(stream))
+    if rc != DGPE_OK:
+        raise DgpeError(rc, load().dgpe_noalloc_last_error().decode())
 
 
 class Solver:
