@@ -151,6 +151,8 @@ def main():
     ap.add_argument("--workload", default="real3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default="both", choices=["both", "fp64", "fp32"],
+                    help="precision forms to time (the first listed is the top-level line)")
     ap.add_argument("--prep-steps", type=int, default=None,
                     help="imaginary-time preparation steps (default: the workload's)")
     args = ap.parse_args()
@@ -213,7 +215,8 @@ def main():
         torch.cuda.synchronize()
 
     forms = {}
-    for fp64 in (True, False):
+    order = {"both": (True, False), "fp64": (True,), "fp32": (False,)}[args.forms]
+    for fp64 in order:
         name = "fp64" if fp64 else "fp32_bulk"
         S = dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64,
                         stream=stream.cuda_stream)
@@ -292,24 +295,26 @@ def main():
         import oracle.build
         oracle.build.build()
         cpu, _, _ = run_oracle_sample(wl)
-    a = forms["fp64"]
-    b = forms["fp32_bulk"]
+    a = forms["fp64"] if "fp64" in forms else forms["fp32_bulk"]
+    b = forms.get("fp32_bulk") if "fp64" in forms else None
     line = {
         "metric": metric, "value": a["value"], "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": a["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": a["dtype"],
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "grid": list(n), "sites": sites, "form": "fp64",
+        "config": {"workload": wl["desc"], "grid": list(n), "sites": sites,
+                   "form": "fp64" if "fp64" in forms else "fp32_bulk",
                    "l2": "inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
                        16 * sites >> 20, 8 * sites >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
                                                       "mu": prep["mu"]}},
         "roofline": a["roofline"], "step_hbm": a["step_hbm"], "passes": a["passes"],
-        "cpu_baseline": cpu, "e2e": a.get("e2e"), "gpu_launches": a["gpu_launches"] + b["gpu_launches"],
+        "cpu_baseline": cpu, "e2e": a.get("e2e"),
+        "gpu_launches": a["gpu_launches"] + (b["gpu_launches"] if b else 0),
         "clocks": a["clocks"], "observables_after": a["observables_after"],
         "fp32_bulk": b,
-        "speedup_fp32_bulk_vs_fp64": b["value"] / a["value"],
+        "speedup_fp32_bulk_vs_fp64": (b["value"] / a["value"]) if b else None,
         "source_hash": source_hash(),
     }
     print(json.dumps(line))
