@@ -54,9 +54,12 @@ def peaks():
 def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1601_04640_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    files = []
+    for dp, _, fs in os.walk(d):
+        files += [os.path.join(dp, f) for f in fs]
+    for f in sorted(files):
+        with open(f, "rb") as fh:
+            h.update(os.path.relpath(f, d).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -151,6 +154,7 @@ def main():
     ap.add_argument("--workload", default="real3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the cuFFT comparison step")
     ap.add_argument("--forms", default="both", choices=["both", "fp64", "fp32"],
                     help="precision forms to time (the first listed is the top-level line)")
     ap.add_argument("--prep-steps", type=int, default=None,
@@ -286,6 +290,34 @@ def main():
         S.close()
         forms[name] = f
 
+    # the paper's design (separate kernels + cuFFT R2C/C2R, one thread per CN
+    # line), same workload and state, timed the same way: comparison only
+    plain = None
+    if not args.no_plain and not imag:
+        try:
+            from paper_1601_04640_gb300 import plain as pl
+            gbuild.build_plain()
+            plain = {}
+            for fp64 in order:
+                name = "fp64" if fp64 else "fp32"
+                with pl.PlainSolver(3, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], fp64,
+                                    stream=stream.cuda_stream) as P:
+                    P.set_psi(psi0)
+                    P.step(args.warmup)
+                    barrier()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    P.step(args.steps)
+                    e1.record(stream)
+                    barrier()
+                    ms = e0.elapsed_time(e1)
+                plain[name] = {"value": world * sites * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps}
+                ours = forms["fp64" if fp64 else "fp32_bulk"]
+                plain[name]["fused_speedup"] = ours["value"] / plain[name]["value"]
+        except Exception as ex:  # the comparison leg must not hide the main result
+            plain = {"unavailable": str(ex)[:200]}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -314,6 +346,7 @@ def main():
         "gpu_launches": a["gpu_launches"] + (b["gpu_launches"] if b else 0),
         "clocks": a["clocks"], "observables_after": a["observables_after"],
         "fp32_bulk": b,
+        "cufft_plain_step": plain,
         "speedup_fp32_bulk_vs_fp64": (b["value"] / a["value"]) if b else None,
         "source_hash": source_hash(),
     }

@@ -162,6 +162,31 @@ int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap);
 const char *dgpe_pass_name(dgpe_t h, int i);
 double dgpe_pass_bytes(dgpe_t h, int i);
 
+/* Reverse mode of one real-time step (the adjoint form: Wirtinger
+ * convention G = 2 dL/dpsi*).  psi_in: device state at the start of step
+ * `step` (complex128 for DGPE_FP64, complex64 for DGPE_FP32_BULK); G: device
+ * buffer of the same type holding G' = 2 dL/dpsi'* for the state after the
+ * step, overwritten with G for psi_in.  Applies C^dagger (Thomas with
+ * conjugated coefficients along z, y, x), the adjoint of the exponential and
+ * one extra dipolar convolution:
+ *   sig = Im(conj(G_phi) e^{-i theta} psi_in),
+ *   G = e^{i theta} G_phi + 2 dt (g sig + g_dd Phi_d[sig]) psi_in,
+ * and adds dt sum sig |psi_in|^2 to *dL_dg and dt sin(m t) sum sig V0 to
+ * dL_dc[m-1] for the current trap modulation (FP64 reductions).  Synchronises.
+ * DGPE_EUNSUPPORTED in imaginary-time mode.  (Differentiation of the step;
+ * the paper computes no gradients.) */
+int dgpe_step_adjoint(dgpe_t h, const void *psi_in, void *G, long long step,
+                      double *dL_dg, double *dL_dc);
+
+/* Fidelity F = |<target|psi(T)>|^2 (inner product h^d sum conj(a) b) after
+ * nsteps real-time steps from psi0 (host FP64 interleaved complex, both), and
+ * its gradient with respect to g and the trap-modulation coefficients c_1..c_M
+ * of dgpe_set_trap_modulation, by a reverse sweep over checkpoints taken every
+ * `every` steps (the states of one segment are recomputed while it is
+ * reversed).  Leaves psi at the last recomputed state.  Synchronises. */
+int dgpe_fidelity_gradient(dgpe_t h, const double *psi0, const double *target, int nsteps,
+                           int every, double *F, double *dF_dg, double *dF_dc);
+
 /* Phi_d of |psi|^2 for a caller's state, computed without allocating any
  * device memory (the paper has no counterpart: this serves callers that must
  * not call cudaMalloc while they run -- work recorded into another

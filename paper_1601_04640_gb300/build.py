@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgpe.so")
+PLAIN_LIB = os.path.join(HERE, "libdgpe_plain.so")
+PLAIN_SRC = os.path.join(CSRC, "plain", "dgpe_plain.cu")
 UNITS = ["dgpe_api.cu", "dgpe_f64.cu", "dgpe_f32.cu", "dgpe_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -34,8 +36,22 @@ def _stale(lib, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_plain(force: bool = False) -> str:
+    """The cuFFT-based comparison step (timed beside the fused path only)."""
+    deps = [PLAIN_SRC, os.path.join(ROOT, "include", "dgpe_plain.h"), os.path.join(ROOT, "include", "dgpe.h")]
+    if not force and not _stale(PLAIN_LIB, deps):
+        return PLAIN_LIB
+    tmp = PLAIN_LIB + ".tmp"
+    cmd = [_nvcc(), *ARCH, *FLAGS, "-shared", "-cudart", "static", PLAIN_SRC, "-o", tmp, "-lcufft"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for the comparison step:\n%s%s" % (r.stdout, r.stderr))
+    os.replace(tmp, PLAIN_LIB)
+    return PLAIN_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))]
+    srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh"))]
     srcs.append(os.path.join(ROOT, "include", "dgpe.h"))
     if not force and not _stale(LIB, srcs):
         return LIB
@@ -52,8 +68,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with ThreadPoolExecutor(max_workers=len(UNITS) + 1) as ex:
+        plain = ex.submit(build_plain, force)
         objs = list(ex.map(compile_unit, UNITS))
+        plain.result()
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

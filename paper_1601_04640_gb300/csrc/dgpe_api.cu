@@ -187,3 +187,17 @@ extern "C" int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap) {
 extern "C" const char *dgpe_pass_name(dgpe_t h, int i) { return h ? h->eng->pass_name(i) : ""; }
 
 extern "C" double dgpe_pass_bytes(dgpe_t h, int i) { return h ? h->eng->pass_bytes(i) : 0.0; }
+
+extern "C" int dgpe_step_adjoint(dgpe_t h, const void *psi_in, void *G, long long step, double *dL_dg,
+                                 double *dL_dc) {
+  CHECK_H(h);
+  if (!psi_in || !G || step < 0) return fail(h, DGPE_EINVAL, "bad arguments");
+  return from_engine(h, h->eng->step_adjoint(psi_in, G, step, dL_dg, dL_dc, h->stream));
+}
+
+extern "C" int dgpe_fidelity_gradient(dgpe_t h, const double *psi0, const double *target, int nsteps,
+                                      int every, double *F, double *dF_dg, double *dF_dc) {
+  CHECK_H(h);
+  if (!psi0 || !target || !F || !dF_dg) return fail(h, DGPE_EINVAL, "NULL argument");
+  return from_engine(h, h->eng->fidelity_gradient(psi0, target, nsteps, every, F, dF_dg, dF_dc, h->stream));
+}

@@ -35,6 +35,10 @@ struct Engine {
   virtual int get_time(long long *step, cudaStream_t s) = 0;
   virtual int launches_per_step() const = 0;
   virtual int profile_steps(int n, double *pass_ms, int cap, cudaStream_t s) = 0;
+  virtual int step_adjoint(const void *psi_in, void *G, long long step, double *dg, double *dc,
+                           cudaStream_t s) = 0;
+  virtual int fidelity_gradient(const double *psi0, const double *target, int nsteps, int every,
+                                double *F, double *dFdg, double *dFdc, cudaStream_t s) = 0;
   virtual const char *pass_name(int i) const = 0;
   virtual double pass_bytes(int i) const = 0;
   virtual size_t sites() const = 0;
@@ -110,6 +114,14 @@ template <typename R> struct EngineT : Engine {
   void *cntab[3] = {nullptr, nullptr, nullptr};
   double *prm = nullptr, *partial = nullptr, *obs_part = nullptr, *dip_part = nullptr, *obs_out = nullptr;
   double2 *stage = nullptr;  // FP64 staging buffer for host transfers (lazy)
+  // reverse-mode buffers (allocated on first use)
+  Cx *adjG = nullptr, *adjT = nullptr;
+  R *adj_phi = nullptr, *adj_sig = nullptr, *adj_ksig = nullptr;
+  double *adj_part = nullptr, *adj_acc = nullptr;
+  void *cntab_adj[3] = {nullptr, nullptr, nullptr};
+  std::vector<Cx *> ckpts, states;
+  double host_cm[16] = {0};
+  int host_M = 0;
   long long *dstep = nullptr;
   unsigned *counter = nullptr;
   FftPlan plx{}, ply{}, plz{}, plx_s{};
@@ -135,9 +147,12 @@ template <typename R> struct EngineT : Engine {
     if (cap) cudaStreamDestroy(cap);
     void *bufs[] = {psi, spec, U, phi_tmp, tw[0], tw[1], tw[2], vt[0], vt[1], vt[2],
                     cntab[0], cntab[1], cntab[2], prm, partial, obs_part, dip_part, obs_out,
-                    dstep, counter, stage};
+                    dstep, counter, stage, adjG, adjT, adj_phi, adj_sig, adj_ksig, adj_part,
+                    adj_acc, cntab_adj[0], cntab_adj[1], cntab_adj[2]};
     for (void *b : bufs)
       if (b) cudaFree(b);
+    for (Cx *b : ckpts) cudaFree(b);
+    for (Cx *b : states) cudaFree(b);
   }
 
   size_t sites() const override { return nsites; }
@@ -337,6 +352,19 @@ template <typename R> struct EngineT : Engine {
         int rc = dalloc((Cx **)&cntab[a], 4 * (size_t)n);
         if (rc) return rc;
       }
+      if (!imag) {
+        // conjugated tables for the reverse step (C^dagger = B^dagger A^-dagger)
+        if (!cntab_adj[a]) {
+          int rc = dalloc((Cx **)&cntab_adj[a], 4 * (size_t)n);
+          if (rc) return rc;
+        }
+        std::vector<Cx> t(4 * (size_t)n);
+        auto put = [&](size_t i, zd v) { t[i].x = (R)v.real(); t[i].y = (R)(-v.imag()); };
+        for (int i = 0; i < n; ++i) {
+          put(i, m[i]); put(n + i, al[i]); put(2 * n + i, P[i]); put(3 * n + i, Q[i]);
+        }
+        DGPE_CK(cudaMemcpy(cntab_adj[a], t.data(), sizeof(Cx) * t.size(), cudaMemcpyHostToDevice));
+      }
       if (imag) {
         std::vector<R> t(4 * (size_t)n);
         for (int i = 0; i < n; ++i) {
@@ -365,6 +393,8 @@ template <typename R> struct EngineT : Engine {
   int set_smem_attrs() {
     int rc;
     if ((rc = smem_attr(k_dens_r2c_x<R, EPT_X>, x_smem))) return rc;
+    if ((rc = smem_attr(k_dens_r2c_x<R, EPT_X, 1>, x_smem))) return rc;
+    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 2>, x_smem))) return rc;
     if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0>, x_smem))) return rc;
     if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0>, x_smem))) return rc;
     if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1>, x_smem))) return rc;
@@ -407,39 +437,54 @@ template <typename R> struct EngineT : Engine {
     DGPE_CK(cudaGetLastError());
     return DGPE_OK;
   }
-  int launch_cn(int axis, bool final_pass, cudaStream_t s) {
+  int launch_cn(int axis, bool final_pass, cudaStream_t s, Cx *buf = nullptr, bool adjoint = false) {
     const CnCfg &c = cn[axis];
     CArgs<R> A{};
-    A.psi = psi; A.cntab = cntab[axis]; A.prm = prm; A.partial = partial; A.counter = counter;
+    A.psi = buf ? buf : psi; A.cntab = adjoint ? cntab_adj[axis] : cntab[axis];
+    A.prm = prm; A.partial = partial; A.counter = counter;
     A.step = dstep; A.estride = c.es; A.ostride = c.os; A.n = c.n; A.ncols = c.ncols; A.W = c.W;
     A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
-    A.norm = (final_pass && imag) ? 1 : 0; A.tau = tau[axis];
+    A.norm = (final_pass && imag) ? 1 : 0; A.tau = adjoint ? -tau[axis] : tau[axis];
     if (imag) k_cn_strided<R, R, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
     else k_cn_strided<R, Cx, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
     DGPE_CK(cudaGetLastError());
     return DGPE_OK;
   }
-  int launch_forward_spectrum(cudaStream_t s) {  // density -> spectrum (x, y)
+  // density (of `src`, or the real field `dens_in`) -> half spectrum along x
+  int launch_forward_spectrum(cudaStream_t s, const Cx *src = nullptr, const R *dens_in = nullptr) {
     XArgs<R> A = xargs();
-    k_dens_r2c_x<R, EPT_X><<<x_grid, x_T, x_smem, s>>>(A);
+    if (src) A.psi = const_cast<Cx *>(src);
+    if (dens_in) {
+      A.dens_in = dens_in;
+      k_dens_r2c_x<R, EPT_X, 1><<<x_grid, x_T, x_smem, s>>>(A);
+    } else {
+      k_dens_r2c_x<R, EPT_X><<<x_grid, x_T, x_smem, s>>>(A);
+    }
     DGPE_CK(cudaGetLastError());
     return DGPE_OK;
   }
-  int launch_p1(int mode, cudaStream_t s) {
+  // mode 0: step pass on psi; 1: Phi_d into phi_out; 2: CN_x (conjugated) on buf
+  int launch_p1(int mode, cudaStream_t s, Cx *buf = nullptr, R *phi_out = nullptr) {
     XArgs<R> A = xargs();
+    if (buf) A.psi = buf;
+    if (phi_out) A.phi_out = phi_out;
     if (mode == 0) {
       if (imag) k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
       else k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
-    } else {
+    } else if (mode == 1) {
       k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1><<<x_grid, x_T, x_smem, s>>>(A);
+    } else {
+      A.cntab = cntab_adj[0];
+      A.tau = -tau[0];
+      k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 2><<<x_grid, x_T, x_smem, s>>>(A);
     }
     DGPE_CK(cudaGetLastError());
     return DGPE_OK;
   }
   // Phi_d chain up to (not including) the C2R along x.
-  int launch_dipolar_chain(cudaStream_t s) {
+  int launch_dipolar_chain(cudaStream_t s, const Cx *src = nullptr, const R *dens_in = nullptr) {
     int rc;
-    if ((rc = launch_forward_spectrum(s))) return rc;
+    if ((rc = launch_forward_spectrum(s, src, dens_in))) return rc;
     if (dim == 3) {
       if ((rc = launch_fft(fy, 0, s))) return rc;
       if ((rc = launch_fft(fz, 2, s))) return rc;
@@ -680,10 +725,131 @@ template <typename R> struct EngineT : Engine {
     double h[17] = {0};
     h[0] = (double)M;
     for (int i = 0; i < M; ++i) h[1 + i] = c[i];
+    host_M = M;
+    for (int i = 0; i < 16; ++i) host_cm[i] = (i < M) ? c[i] : 0.0;
     DGPE_CK(cudaMemcpyAsync(prm + PRM_M, h, sizeof(h), cudaMemcpyHostToDevice, s));
     DGPE_CK(cudaStreamSynchronize(s));
     return DGPE_OK;
   }
+  // ---------------------------------------------------------- reverse mode
+  int adj_alloc() {
+    int rc;
+    if (!adjG && (rc = dalloc(&adjG, nsites))) return rc;
+    if (!adjT && (rc = dalloc(&adjT, nsites))) return rc;
+    if (!adj_phi && (rc = dalloc(&adj_phi, nsites))) return rc;
+    if (!adj_sig && (rc = dalloc(&adj_sig, nsites))) return rc;
+    if (!adj_ksig && (rc = dalloc(&adj_ksig, nsites))) return rc;
+    if (!adj_part && (rc = dalloc(&adj_part, 2 * 152 * 8))) return rc;
+    if (!adj_acc && (rc = dalloc(&adj_acc, 17))) return rc;
+    return DGPE_OK;
+  }
+  // One reverse step on device buffers; contributions added to adj_acc.
+  int adjoint_on_device(const Cx *pin, Cx *G, long long st, cudaStream_t s) {
+    int rc;
+    // G_phi = C_x^dagger C_y^dagger C_z^dagger G'
+    if (dim == 3 && (rc = launch_cn(2, false, s, G, true))) return rc;
+    if ((rc = launch_cn(1, false, s, G, true))) return rc;
+    if ((rc = launch_p1(2, s, G))) return rc;
+    // Phi_d of the step-start state
+    if (has_dip) {
+      if ((rc = launch_dipolar_chain(s, pin))) return rc;
+      if ((rc = launch_p1(1, s, nullptr, adj_phi))) return rc;
+    } else {
+      DGPE_CK(cudaMemsetAsync(adj_phi, 0, sizeof(R) * nsites, s));
+    }
+    const double t = (double)st * p.dt;
+    double sm = 1.0;
+    for (int m = 1; m <= host_M; ++m) sm += host_cm[m - 1] * std::sin((double)m * t);
+    AArgs<R> A{};
+    A.psi_in = pin; A.G = G; A.phi = adj_phi; A.sig = adj_sig; A.ksig = adj_ksig; A.sig_out = adj_sig;
+    A.vx = vt[0]; A.vy = vt[1]; A.vz = vt[2]; A.partial = adj_part; A.nx = nx; A.ny = ny; A.dim = dim;
+    A.n = nsites; A.dts = p.dt * sm; A.gdt = p.dt * p.g; A.gdddt = p.dt * p.gdd;
+    A.two_dt_g = 2.0 * p.dt * p.g; A.two_dt_gdd = 2.0 * p.dt * p.gdd;
+    const int nblk = 152 * 8;
+    k_adj_sigma<R><<<nblk, 256, 0, s>>>(A);
+    k_adj_accumulate<<<1, 256, 0, s>>>(adj_part, nblk, adj_acc, p.dt, t, host_M);
+    DGPE_CK(cudaGetLastError());
+    if (has_dip) {
+      if ((rc = launch_dipolar_chain(s, nullptr, adj_sig))) return rc;
+      if ((rc = launch_p1(1, s, nullptr, adj_ksig))) return rc;
+    } else {
+      DGPE_CK(cudaMemsetAsync(adj_ksig, 0, sizeof(R) * nsites, s));
+    }
+    k_adj_update<R><<<nblk, 256, 0, s>>>(A);
+    DGPE_CK(cudaGetLastError());
+    return DGPE_OK;
+  }
+  int step_adjoint(const void *psi_in, void *G, long long st, double *dg, double *dc,
+                   cudaStream_t s) override {
+    if (imag) { err = "the reverse step is defined for real time"; return DGPE_EUNSUPPORTED; }
+    int rc = adj_alloc();
+    if (rc) return rc;
+    DGPE_CK(cudaMemsetAsync(adj_acc, 0, 17 * sizeof(double), s));
+    if ((rc = adjoint_on_device((const Cx *)psi_in, (Cx *)G, st, s))) return rc;
+    double acc[17];
+    DGPE_CK(cudaMemcpyAsync(acc, adj_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    if (dg) *dg += acc[0];
+    if (dc) for (int m = 0; m < host_M; ++m) dc[m] += acc[1 + m];
+    return DGPE_OK;
+  }
+  // F = |<target|psi(T)>|^2 (h^d inner product) after nsteps steps from psi0,
+  // and dF/dg, dF/dc_m by the reverse sweep with checkpoints every `every`
+  // steps (states of one segment recomputed and kept while it is reversed).
+  int fidelity_gradient(const double *psi0, const double *target, int nsteps, int every,
+                        double *F, double *dFdg, double *dFdc, cudaStream_t s) override {
+    if (imag) { err = "the reverse step is defined for real time"; return DGPE_EUNSUPPORTED; }
+    if (nsteps < 1 || every < 1) { err = "nsteps and every must be >= 1"; return DGPE_EINVAL; }
+    int rc = adj_alloc();
+    if (rc) return rc;
+    const int nseg = (nsteps + every - 1) / every;
+    while ((int)ckpts.size() < nseg) { Cx *b = nullptr; if ((rc = dalloc(&b, nsites))) return rc; ckpts.push_back(b); }
+    while ((int)states.size() < every) { Cx *b = nullptr; if ((rc = dalloc(&b, nsites))) return rc; states.push_back(b); }
+    // target into adjT (stored precision)
+    if ((rc = set_psi_host(target, s))) return rc;
+    DGPE_CK(cudaMemcpyAsync(adjT, psi, sizeof(Cx) * nsites, cudaMemcpyDeviceToDevice, s));
+    if ((rc = set_psi_host(psi0, s))) return rc;
+    // forward with checkpoints
+    for (int j = 0; j < nseg; ++j) {
+      DGPE_CK(cudaMemcpyAsync(ckpts[j], psi, sizeof(Cx) * nsites, cudaMemcpyDeviceToDevice, s));
+      const int len = std::min(every, nsteps - j * every);
+      if ((rc = step(len, s))) return rc;
+    }
+    // c = h^d sum conj(target) psi_T, F = |c|^2, G_T = 2 h^d c target
+    const int nblk = 152 * 8;
+    k_cdot<R><<<nblk, 256, 0, s>>>(adjT, psi, nsites, adj_part);
+    DGPE_CK(cudaGetLastError());
+    std::vector<double> part(2 * nblk);
+    DGPE_CK(cudaMemcpyAsync(part.data(), adj_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    double cr = 0.0, ci = 0.0;
+    for (int i = 0; i < nblk; ++i) { cr += part[2 * i]; ci += part[2 * i + 1]; }
+    const double cell = p.h[0] * p.h[1] * (dim == 3 ? p.h[2] : 1.0);
+    cr *= cell; ci *= cell;
+    *F = cr * cr + ci * ci;
+    k_cscale<R><<<nblk, 256, 0, s>>>(adjG, adjT, 2.0 * cell * cr, 2.0 * cell * ci, nsites);
+    DGPE_CK(cudaMemsetAsync(adj_acc, 0, 17 * sizeof(double), s));
+    // reverse sweep
+    for (int j = nseg - 1; j >= 0; --j) {
+      const int len = std::min(every, nsteps - j * every);
+      DGPE_CK(cudaMemcpyAsync(psi, ckpts[j], sizeof(Cx) * nsites, cudaMemcpyDeviceToDevice, s));
+      long long st0 = (long long)j * every;
+      DGPE_CK(cudaMemcpyAsync(dstep, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+      for (int i = 0; i < len; ++i) {
+        DGPE_CK(cudaMemcpyAsync(states[i], psi, sizeof(Cx) * nsites, cudaMemcpyDeviceToDevice, s));
+        if (i + 1 < len && (rc = step(1, s))) return rc;
+      }
+      for (int i = len - 1; i >= 0; --i)
+        if ((rc = adjoint_on_device(states[i], adjG, st0 + i, s))) return rc;
+    }
+    double acc[17];
+    DGPE_CK(cudaMemcpyAsync(acc, adj_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    *dFdg = acc[0];
+    if (dFdc) for (int m = 0; m < host_M; ++m) dFdc[m] = acc[1 + m];
+    return DGPE_OK;
+  }
+
   int set_time(long long st, cudaStream_t s) override {
     DGPE_CK(cudaMemcpyAsync(dstep, &st, sizeof(st), cudaMemcpyHostToDevice, s));
     DGPE_CK(cudaStreamSynchronize(s));

@@ -34,6 +34,7 @@ template <typename R> struct XArgs {  // x-line passes
   cx<R> *psi;
   cx<R> *spec;
   R *phi_out;
+  const R *dens_in;  // P4 with SRC = 1: transform this real field instead of |psi|^2
   const double *prm;
   const long long *step;
   const cx<R> *tw;
@@ -141,7 +142,8 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 // Every pass is launched with at most DGPE_MAXT threads per block.
 #define DGPE_MAXT 256
 
-template <typename R, int EPT>
+// SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
+template <typename R, int EPT, int SRC = 0>
 __global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
@@ -154,8 +156,13 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
   auto load = [&](int l, int a) -> cx<R> {
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     R d0 = 0, d1 = 0;
-    if (r0 < nrows) { cx<R> v = psi[(size_t)r0 * n + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
-    if (r1 < nrows) { cx<R> v = psi[(size_t)r1 * n + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
+    if (SRC == 1) {
+      if (r0 < nrows) d0 = A.dens_in[(size_t)r0 * n + a];
+      if (r1 < nrows) d1 = A.dens_in[(size_t)r1 * n + a];
+    } else {
+      if (r0 < nrows) { cx<R> v = psi[(size_t)r0 * n + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
+      if (r1 < nrows) { cx<R> v = psi[(size_t)r1 * n + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
+    }
     return mk<R>(d0, d1);
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
@@ -177,6 +184,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
 
 // ------------------------------------------------------------------ P1
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
+// MODE 2: CN_x alone (the reverse step applies it to the adjoint field).
 template <typename R, typename Coef, int EPT, int CL, int MODE>
 __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -188,7 +196,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
   const int ln = ilog2(n), lny = ilog2(A.ny);
   const int p0 = blockIdx.x * A.LP;
   const int T = blockDim.x, t = threadIdx.x;
-  if (MODE == 0) {
+  if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
     // every load of the tile is issued before any is used (2 LP n = CL T)
     cx<R> buf[CL];
@@ -224,7 +232,9 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
     const R th = dts * V + gdt * dens + gdddt * phi;
     pt[ia] = nonlinear_factor<R>(v, th, imag);
   };
-  if (A.has_dip) {
+  if (MODE == 2) {
+    __syncthreads();
+  } else if (A.has_dip) {
     auto load = [&](int l, int a) -> cx<R> {
       const int r0 = 2 * (p0 + l), r1 = r0 + 1;
       const int k = (a <= nh) ? a : n - a;
@@ -455,6 +465,109 @@ static __global__ void k_obs_final(const double *site_partial, int nsite_blocks,
   for (int i = threadIdx.x; i < ndip; i += blockDim.x) s += dip_partial[i];
   s = block_sum(s, red);
   if (threadIdx.x == 0) out[OBS_COUNT] = s;
+}
+
+// ------------------------------------------------------------- adjoint
+// Reverse step of one real-time step psi' = C e^{-i theta} psi (G = 2 dL/dpsi*):
+//   sig = Im(conj(G_phi) phi), phi = e^{-i theta} psi_in, G_phi = C^dagger G';
+//   G = e^{+i theta} G_phi + 2 dt (g sig + g_dd K*sig) psi_in;
+//   dL/dg += dt sum sig n,  dL/dc_m += dt sin(m t) sum sig V0.
+template <typename R> struct AArgs {
+  const cx<R> *psi_in;
+  cx<R> *G;
+  const R *phi, *sig, *ksig;
+  R *sig_out;
+  const R *vx, *vy, *vz;
+  double *partial;  // [block][2]: sum sig n, sum sig V0
+  int nx, ny, dim;
+  size_t n;
+  double dts, gdt, gdddt, two_dt_g, two_dt_gdd;
+};
+
+template <typename R> __device__ __forceinline__ R adj_theta(const AArgs<R> &A, size_t i, cx<R> v, R *dens, R *v0) {
+  const int x = (int)(i % A.nx);
+  const size_t r = i / A.nx;
+  const int y = (int)(r % A.ny), z = (int)(r / A.ny);
+  *dens = v.x * v.x + v.y * v.y;
+  *v0 = A.vx[x] + A.vy[y] + A.vz[z];
+  return (R)A.dts * *v0 + (R)A.gdt * *dens + (R)A.gdddt * A.phi[i];
+}
+
+template <typename R>
+__global__ void k_adj_sigma(AArgs<R> A) {
+  __shared__ double red[32];
+  double sn = 0.0, sv = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.n; i += (size_t)gridDim.x * blockDim.x) {
+    const cx<R> v = A.psi_in[i];
+    R dens, v0;
+    const R th = adj_theta(A, i, v, &dens, &v0);
+    R s, c;
+    fsincos(th, &s, &c);
+    const cx<R> ph = mk<R>(v.x * c + v.y * s, v.y * c - v.x * s);  // e^{-i th} psi
+    const cx<R> g = A.G[i];
+    const R sig = g.x * ph.y - g.y * ph.x;  // Im(conj(g) ph)
+    A.sig_out[i] = sig;
+    sn += (double)sig * dens;
+    sv += (double)sig * v0;
+  }
+  sn = block_sum(sn, red);
+  if (threadIdx.x == 0) A.partial[2 * blockIdx.x] = sn;
+  sv = block_sum(sv, red);
+  if (threadIdx.x == 0) A.partial[2 * blockIdx.x + 1] = sv;
+}
+
+template <typename R>
+__global__ void k_adj_update(AArgs<R> A) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.n; i += (size_t)gridDim.x * blockDim.x) {
+    const cx<R> v = A.psi_in[i];
+    R dens, v0;
+    const R th = adj_theta(A, i, v, &dens, &v0);
+    R s, c;
+    fsincos(th, &s, &c);
+    const cx<R> g = A.G[i];
+    const R f = (R)A.two_dt_g * A.sig[i] + (R)A.two_dt_gdd * A.ksig[i];
+    // e^{+i th} G_phi + f psi_in
+    A.G[i] = mk<R>(g.x * c - g.y * s + f * v.x, g.y * c + g.x * s + f * v.y);
+  }
+}
+
+// Fixed-order totals of the per-block partials, accumulated in FP64:
+// acc[0] += dt S_n,  acc[1 + m - 1] += dt sin(m t) S_V.
+static __global__ void k_adj_accumulate(const double *partial, int nblk, double *acc, double dt, double t, int M) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) { a += partial[2 * i]; b += partial[2 * i + 1]; }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    acc[0] += dt * a;
+    for (int m = 1; m <= M; ++m) acc[m] += dt * sin((double)m * t) * b;
+  }
+}
+
+// partial[block] = sum conj(a) b (complex, FP64)
+template <typename R>
+__global__ void k_cdot(const cx<R> *a, const cx<R> *b, size_t n, double *partial) {
+  __shared__ double red[32];
+  double re = 0.0, im = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cx<R> u = a[i], v = b[i];
+    re += (double)u.x * v.x + (double)u.y * v.y;
+    im += (double)u.x * v.y - (double)u.y * v.x;
+  }
+  re = block_sum(re, red);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x] = re;
+  im = block_sum(im, red);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = im;
+}
+
+// out = (cr + i ci) * in
+template <typename R>
+__global__ void k_cscale(cx<R> *out, const cx<R> *in, double cr, double ci, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cx<R> v = in[i];
+    out[i] = mk<R>((R)(cr * v.x - ci * v.y), (R)(cr * v.y + ci * v.x));
+  }
 }
 
 // --------------------------------------------------------- state transfer

@@ -41,6 +41,7 @@ EXPORTS = [
     "dgpe_get_time", "dgpe_sync", "dgpe_launches_per_step", "dgpe_last_error",
     "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes",
     "dgpe_dipolar_potential_noalloc", "dgpe_noalloc_last_error",
+    "dgpe_step_adjoint", "dgpe_fidelity_gradient",
 ]
 
 
@@ -306,3 +307,40 @@ class Solver:
 
     def sync(self):
         dgpe_sync(self.h)
+
+
+# ------------------------------------------------------------- reverse mode
+def _bind_adjoint():
+    lib = load()
+    if not getattr(lib, "_adj_bound", False):
+        lib.dgpe_step_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.dgpe_fidelity_gradient.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double)]
+        lib._adj_bound = True
+    return lib
+
+
+def dgpe_step_adjoint(h, psi_in_ptr: int, G_ptr: int, step: int, M: int = 0):
+    """Pull G back through one real-time step (device buffers); returns the
+    step's (dL/dg, [dL/dc_m]) contributions."""
+    lib = _bind_adjoint()
+    dg = C.c_double(0.0)
+    dc = (C.c_double * 16)()
+    _check(lib.dgpe_step_adjoint(h, C.c_void_p(psi_in_ptr), C.c_void_p(G_ptr), int(step),
+                                 C.byref(dg), dc), h)
+    return dg.value, [dc[i] for i in range(M)]
+
+
+def dgpe_fidelity_gradient(h, psi0, target, nsteps: int, every: int, M: int = 0):
+    """(F, dF/dg, [dF/dc_m]) for F = |<target|psi(T)>|^2 after nsteps steps."""
+    lib = _bind_adjoint()
+    a = np.ascontiguousarray(psi0, dtype=np.complex128)
+    b = np.ascontiguousarray(target, dtype=np.complex128)
+    F = C.c_double(0.0)
+    dg = C.c_double(0.0)
+    dc = (C.c_double * 16)()
+    _check(lib.dgpe_fidelity_gradient(h, a.ctypes.data, b.ctypes.data, int(nsteps), int(every),
+                                      C.byref(F), C.byref(dg), dc), h)
+    return F.value, dg.value, [dc[i] for i in range(M)]

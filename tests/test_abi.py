@@ -12,13 +12,22 @@ from paper_1601_04640_gb300 import dgpe
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    names = set()
-    for f in os.listdir(os.path.join(ROOT, "include")):
-        if f.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", f)).read()
-            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dgpe_\w+)\s*\(", src, re.M))
-    return names
+def _declared(header="dgpe.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dgpe_\w+)\s*\(", src, re.M))
+
+
+def test_every_header_is_checked():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == [
+        "dgpe.h", "dgpe_plain.h"]
+
+
+def test_comparison_library_exports(lib):
+    plain = ctypes.CDLL(gbuild.PLAIN_LIB)
+    names = _declared("dgpe_plain.h")
+    assert "dgpe_plain_step" in names
+    for n in sorted(names):
+        assert hasattr(plain, n), n
 
 
 @pytest.fixture(scope="module")
