@@ -187,6 +187,27 @@ int dgpe_step_adjoint(dgpe_t h, const void *psi_in, void *G, long long step,
 int dgpe_fidelity_gradient(dgpe_t h, const double *psi0, const double *target, int nsteps,
                            int every, double *F, double *dF_dg, double *dF_dc);
 
+/* ---- Batched form: many independent 2D XY condensates stepped together ----
+ * (the paper's imag2dXY / real2dXY programs, one problem each; here a
+ * parameter sweep).  ps[0..count-1]: dim 2, plane XY, square grids
+ * (nx == ny, any supported length), precision DGPE_FP32_BULK, kernel
+ * QUASI2D_XY, imaginary or real time each.  Problems of equal size and mode
+ * form a class; each class runs the four 2D passes as batched kernels (one
+ * problem per grid z-index) with a tile schedule chosen at create time by
+ * timing candidates; one step of all classes is one captured CUDA graph.
+ * States start at zero; problem i is addressed by its index. */
+typedef struct dgpe_batch *dgpe_batch_t;
+int dgpe_batch_create(const dgpe_params *ps, int count, void *cuda_stream, dgpe_batch_t *out);
+void dgpe_batch_destroy(dgpe_batch_t b);
+int dgpe_batch_set_psi(dgpe_batch_t b, int i, const double *psi, size_t n_sites);
+int dgpe_batch_get_psi(dgpe_batch_t b, int i, double *psi, size_t n_sites);   /* synchronises */
+int dgpe_batch_step(dgpe_batch_t b, int n);                                    /* n graph replays */
+int dgpe_batch_observables(dgpe_batch_t b, int i, dgpe_obs *o);                /* synchronises */
+/* number of classes, total sites, algorithmic HBM bytes of one step */
+int dgpe_batch_info(dgpe_batch_t b, int *classes, long long *sites, double *bytes_per_step);
+int dgpe_batch_launches_per_step(dgpe_batch_t b);
+const char *dgpe_batch_last_error(dgpe_batch_t b);
+
 /* Phi_d of |psi|^2 for a caller's state, computed without allocating any
  * device memory (the paper has no counterpart: this serves callers that must
  * not call cudaMalloc while they run -- work recorded into another

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgpe.so")
 PLAIN_LIB = os.path.join(HERE, "libdgpe_plain.so")
 PLAIN_SRC = os.path.join(CSRC, "plain", "dgpe_plain.cu")
-UNITS = ["dgpe_api.cu", "dgpe_f64.cu", "dgpe_f32.cu", "dgpe_noalloc.cu"]
+UNITS = ["dgpe_api.cu", "dgpe_f64.cu", "dgpe_f32.cu", "dgpe_noalloc.cu", "dgpe_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]

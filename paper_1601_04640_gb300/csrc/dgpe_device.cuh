@@ -217,47 +217,57 @@ template <int PADW> __device__ __forceinline__ int sidx(int l, int a, int SL, in
   return l * SL + a * SA;
 }
 
-// One Stockham stage with radix RAD over `nlines` lines of length n (2^ln)
-// held in shared memory.  Butterfly j of a line reads elements j + r n/RAD,
-// twiddles them by w_{Ns RAD}^{(j mod Ns) r}, applies the RAD-point DFT and
-// writes element (j / Ns) Ns RAD + (j mod Ns) + r Ns.  The first stage reads
-// through `load` instead of shared memory and the last writes through `store`
-// (its outputs are in natural order).  Each thread owns EPT / RAD butterflies,
-// so all of its values stay in registers across the barrier that separates
-// the reads from the writes (in-place update).
-template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, class Load, class Store>
-__device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines, int ln, int lNs,
-                                          bool first, bool last, const cx<R> *__restrict__ tw,
-                                          Load &load, Store &store) {
+// Index arithmetic of one Stockham stage.  POW2: n, nlines and Ns are powers
+// of two and the stage uses shifts and masks; otherwise divisions.
+struct StageIdx {
+  int n, nbl, nlines, Ns, ln, lnbl, lnl, lNs, lr;
+};
+
+// One Stockham stage with radix RAD over `nlines` lines of length n held in
+// shared memory.  Butterfly j of a line reads elements j + r n/RAD, twiddles
+// them by w_{Ns RAD}^{(j mod Ns) r}, applies the RAD-point DFT and writes
+// element (j / Ns) Ns RAD + (j mod Ns) + r Ns.  The first stage reads through
+// `load` instead of shared memory and the last writes through `store` (its
+// outputs are in natural order).  Each thread owns EPT / RAD butterflies, so
+// all of its values stay in registers across the barrier that separates the
+// reads from the writes (in-place update).
+template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, bool POW2, class Load, class Store>
+__device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const StageIdx &I, bool first,
+                                          bool last, const cx<R> *__restrict__ tw, Load &load,
+                                          Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
-  constexpr int LR = Log2<RAD>::value;
   const int T = blockDim.x, t = threadIdx.x;
-  const int lnbl = ln - LR, nbl = 1 << lnbl;
+  const int nbl = I.nbl, nlines = I.nlines, Ns = I.Ns;
   const int B = nbl * nlines;
-  const int lnl = LINE_FAST ? ilog2(nlines) : 0;
-  const int Ns = 1 << lNs;
-  const int tshift = ln - lNs - LR;  // twiddle stride n / (Ns RAD)
+  const int tstride = I.n / (Ns * RAD);  // twiddle stride n / (Ns RAD)
+  auto line_of = [&](int b) {
+    if (POW2) return LINE_FAST ? (b & (nlines - 1)) : (b >> I.lnbl);
+    return LINE_FAST ? (b % nlines) : (b / nbl);
+  };
+  auto bfly_of = [&](int b) {
+    if (POW2) return LINE_FAST ? (b >> I.lnl) : (b & (nbl - 1));
+    return LINE_FAST ? (b / nlines) : (b % nbl);
+  };
   cx<R> v[EPT];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     const bool ok = b < B;
-    const int l = LINE_FAST ? (b & (nlines - 1)) : (b >> lnbl);
-    const int j = LINE_FAST ? (b >> lnl) : (b & (nbl - 1));
+    const int l = line_of(b), j = bfly_of(b);
     cx<R> *u = v + i * RAD;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-      const int a = j + (r << lnbl);
+      const int a = j + r * nbl;
       if (!ok) u[r] = czero<cx<R>>();
       else if (first) u[r] = load(l, a);
       else u[r] = sm[sidx<PADW>(l, a, SL, SA)];
     }
     if (!first) {
-      const int k = j & (Ns - 1);
+      const int k = POW2 ? (j & (Ns - 1)) : (j % Ns);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        cx<R> w = tw[(k * r) << tshift];
+        cx<R> w = tw[k * r * tstride];
         u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
       }
     }
@@ -268,13 +278,13 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines,
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     if (b < B) {
-      const int l = LINE_FAST ? (b & (nlines - 1)) : (b >> lnbl);
-      const int j = LINE_FAST ? (b >> lnl) : (b & (nbl - 1));
-      const int base = ((j >> lNs) << (lNs + LR)) + (j & (Ns - 1));
+      const int l = line_of(b), j = bfly_of(b);
+      const int base = POW2 ? (((j >> I.lNs) << (I.lNs + I.lr)) + (j & (Ns - 1)))
+                            : ((j / Ns) * Ns * RAD + (j % Ns));
       cx<R> *u = v + i * RAD;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
-        const int a = base + (r << lNs);
+        const int a = base + r * Ns;
         if (last) store(l, a, u[r]);
         else sm[sidx<PADW>(l, a, SL, SA)] = u[r];
       }
@@ -284,21 +294,33 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, int nlines,
 }
 
 // Full transform of every line of the tile.  tw[t] = exp(-2 pi i t / n).
-template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, class Load, class Store>
+template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, bool POW2 = true, class Load, class Store>
 __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
                          const cx<R> *__restrict__ tw, Load load, Store store) {
-  const int ln = ilog2(pl.n);
-  int lNs = 0;
+  StageIdx I;
+  I.n = pl.n;
+  I.nlines = nlines;
+  I.Ns = 1;
+  I.ln = POW2 ? ilog2(pl.n) : 0;
+  I.lnl = (POW2 && LINE_FAST) ? ilog2(nlines) : 0;
+  I.lNs = 0;
   for (int s = 0; s < pl.ns; ++s) {
     const int rad = INV ? pl.rad[pl.ns - 1 - s] : pl.rad[s];
     const bool first = (s == 0), last = (s == pl.ns - 1);
+    I.nbl = pl.n / rad;
+    I.lr = (rad == 2) ? 1 : (rad == 4) ? 2 : (rad == 8) ? 3 : (rad == 16) ? 4 : 0;
+    I.lnbl = I.ln - I.lr;
     switch (rad) {
-      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 1; break;
-      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 2; break;
-      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 3; break;
-      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST, PADW>(sm, SL, SA, nlines, ln, lNs, first, last, tw, load, store); lNs += 4; break;
+      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 3: if constexpr (EPT % 3 == 0 && !POW2) fft_stage<R, EPT, 3, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 5: if constexpr (EPT % 5 == 0 && !POW2) fft_stage<R, EPT, 5, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
       default: break;
     }
+    I.Ns *= rad;
+    I.lNs += I.lr;
   }
 }
 

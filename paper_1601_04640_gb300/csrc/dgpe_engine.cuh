@@ -4,8 +4,10 @@
 // capture.  Instantiated for double (FP64 form) and float (FP32-bulk form).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
+#include <type_traits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -48,6 +50,10 @@ struct Engine {
 Engine *make_engine_f64();
 Engine *make_engine_f32();
 
+// Everything below has internal linkage: each translation unit gets its own
+// solver template and kernels (see dgpe_kernels.cuh).
+namespace {
+
 // ----------------------------------------------------------- host helpers
 // Radix sequence for length n whose radices divide ept (largest first).
 inline bool make_plan(int n, int ept, FftPlan &pl) {
@@ -65,6 +71,49 @@ inline bool make_plan(int n, int ept, FftPlan &pl) {
   }
   return m == 1 && pl.ns > 0;
 }
+
+// Kernel variant of one axis length n: CN chunk length CL (n / CL lanes per
+// line, a power of two <= 32), elements per thread of the x-line and strided
+// FFTs, and whether n is a power of two (shift/mask index arithmetic).
+//   powers of two: CL 16, EPT_X 8, EPT_S 8 (FP64) / 16 (FP32)
+//   3 * 2^k:       CL 12, EPT_X 12, EPT_S 12  (radices 4, 3, 2)
+//   5 * 2^k:       CL 10, EPT_X 20, EPT_S 20  (radices 5, 4, 2)
+enum { VAR_P2 = 0, VAR_3 = 1, VAR_5 = 2, VAR_NONE = -1 };
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+inline int axis_variant(int n) {
+  if (is_pow2(n) && n >= 32 && n <= 512) return VAR_P2;
+  if (n % 3 == 0 && is_pow2(n / 3) && n / 12 >= 1 && n / 12 <= 32 && n % 12 == 0) return VAR_3;
+  if (n % 5 == 0 && is_pow2(n / 5) && n % 10 == 0 && n / 10 <= 32) return VAR_5;
+  return VAR_NONE;
+}
+inline int variant_cl(int v) { return v == VAR_P2 ? 16 : v == VAR_3 ? 12 : 10; }
+
+// Call f(CL, EPT_X, POW2) with compile-time constants for variant v.
+template <class F> int with_xvar(int v, F &&f) {
+  switch (v) {
+    case VAR_P2: return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 8>{}, std::true_type{});
+    case VAR_3: return f(std::integral_constant<int, 12>{}, std::integral_constant<int, 12>{}, std::false_type{});
+    default: return f(std::integral_constant<int, 10>{}, std::integral_constant<int, 20>{}, std::false_type{});
+  }
+}
+// Call f(EPT_S, POW2) for the strided FFT of variant v (pow2 EPT_S given).
+template <int EPTP2, class F> int with_svar(int v, F &&f) {
+  switch (v) {
+    case VAR_P2: return f(std::integral_constant<int, EPTP2>{}, std::true_type{});
+    case VAR_3: return f(std::integral_constant<int, 12>{}, std::false_type{});
+    default: return f(std::integral_constant<int, 20>{}, std::false_type{});
+  }
+}
+// Call f(CL) for the CN chunk of variant v.
+template <class F> int with_cl(int v, F &&f) {
+  switch (v) {
+    case VAR_P2: return f(std::integral_constant<int, 16>{});
+    case VAR_3: return f(std::integral_constant<int, 12>{});
+    default: return f(std::integral_constant<int, 10>{});
+  }
+}
+inline int variant_ept_x(int v) { return v == VAR_P2 ? 8 : v == VAR_3 ? 12 : 20; }
+inline int variant_ept_s(int v, int p2) { return v == VAR_P2 ? p2 : v == VAR_3 ? 12 : 20; }
 
 // erfcx(u) = exp(u^2) erfc(u) for u >= 0; continued asymptotic series where
 // erfc underflows.
@@ -84,6 +133,15 @@ inline double wavenumber(int j, int n, double h) {
   return 2.0 * M_PI * (double)jj / ((double)n * h);
 }
 
+#define DGPE_LCK(name)                                                       \
+  do {                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                     \
+    if (e_ != cudaSuccess) {                                                 \
+      err = std::string("launch of ") + (name) + ": " + cudaGetErrorString(e_); \
+      return DGPE_ECUDA;                                                     \
+    }                                                                        \
+  } while (0)
+
 #define DGPE_CK(call)                                                        \
   do {                                                                       \
     cudaError_t e_ = (call);                                                 \
@@ -95,9 +153,8 @@ inline double wavenumber(int j, int n, double h) {
 
 template <typename R> struct EngineT : Engine {
   typedef cx<R> Cx;
-  static constexpr int EPT_X = 8;                  // x-pass elements per thread
-  static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFT passes
-  static constexpr int CMAX = 16;                  // CN chunk length (every axis)
+  static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFTs, power-of-two lengths
+  int var[3] = {VAR_P2, VAR_P2, VAR_P2};           // kernel variant per axis
   static constexpr int PW = 128 / (int)sizeof(Cx); // pad period of line-major tiles
   static constexpr int W = 128 / (int)sizeof(Cx);  // columns per strided tile (128 B)
 
@@ -188,10 +245,18 @@ template <typename R> struct EngineT : Engine {
     ncol_spec = nx / 2 + 1;
     nspec = (size_t)px * nrows;
 
-    // FFT plans
-    if (!make_plan(nx, EPT_X, plx) || !make_plan(ny, EPT_S, ply) ||
-        (dim == 3 && !make_plan(nz, EPT_S, plz))) {
-      err = "grid size not supported by the FFT plans (use powers of two 16..512)";
+    // kernel variants and FFT plans
+    const int nsz[3] = {nx, ny, nz};
+    for (int a = 0; a < dim; ++a) {
+      var[a] = axis_variant(nsz[a]);
+      if (var[a] == VAR_NONE) {
+        err = "grid length not supported (powers of two, 3*2^k or 5*2^k, 32..512)";
+        return DGPE_EUNSUPPORTED;
+      }
+    }
+    if (!make_plan(nx, variant_ept_x(var[0]), plx) || !make_plan(ny, variant_ept_s(var[1], EPT_S), ply) ||
+        (dim == 3 && !make_plan(nz, variant_ept_s(var[2], EPT_S), plz))) {
+      err = "grid size not supported by the FFT plans";
       return DGPE_EUNSUPPORTED;
     }
     int rc;
@@ -237,8 +302,8 @@ template <typename R> struct EngineT : Engine {
     if (has_dip && (rc = build_kernel_table())) return rc;
 
     // configurations
-    x_C = CMAX;
-    if (nx % x_C) { err = "nx must be a multiple of 16"; return DGPE_EUNSUPPORTED; }
+    x_C = variant_cl(var[0]);
+    if (nx % x_C) { err = "nx is not a multiple of the CN chunk"; return DGPE_EUNSUPPORTED; }
     x_TPL = nx / x_C;
     if (x_TPL > 32) { err = "nx > 512 not supported"; return DGPE_EUNSUPPORTED; }
     x_LP = std::max(1, (sizeof(R) == 8 ? 64 : DGPE_MAXT / 2) / x_TPL);
@@ -257,12 +322,19 @@ template <typename R> struct EngineT : Engine {
     fz.axis = 2;
     if (has_dip) {
       // y transform over the spectrum
-      // tile width W columns (128 B rows), narrowed so blocks stay <= DGPE_MAXT
-      auto wfor = [&](int n) { return std::max(1, std::min(W, DGPE_MAXT * EPT_S / n)); };
-      fy.n = ny; fy.W = wfor(ny); fy.T = fy.W * ny / EPT_S; fy.es = px; fy.os = (long long)ny * px;
+      // tile width W columns (128 B rows), narrowed (by powers of two) so
+      // blocks stay <= DGPE_MAXT threads
+      auto wfor = [&](int n, int ept) {
+        int w = W;
+        while (w > 1 && w * n / ept > DGPE_MAXT) w >>= 1;
+        return w;
+      };
+      const int ey = variant_ept_s(var[1], EPT_S);
+      fy.n = ny; fy.W = wfor(ny, ey); fy.T = fy.W * ny / ey; fy.es = px; fy.os = (long long)ny * px;
       fy.grid = dim3((ncol_spec + fy.W - 1) / fy.W, nz); fy.smem = sizeof(Cx) * (size_t)ny * fy.W; fy.pl = ply;
       if (dim == 3) {
-        fz.n = nz; fz.W = wfor(nz); fz.T = fz.W * nz / EPT_S; fz.es = (long long)ny * px; fz.os = px;
+        const int ez = variant_ept_s(var[2], EPT_S);
+        fz.n = nz; fz.W = wfor(nz, ez); fz.T = fz.W * nz / ez; fz.es = (long long)ny * px; fz.os = px;
         fz.grid = dim3((ncol_spec + fz.W - 1) / fz.W, ny); fz.smem = sizeof(Cx) * (size_t)nz * fz.W; fz.pl = plz;
       }
       if (fy.T > DGPE_MAXT || fz.T > DGPE_MAXT) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
@@ -272,7 +344,9 @@ template <typename R> struct EngineT : Engine {
     const FtCfg &last = (dim == 3) ? fz : fy;
     ndip = has_dip ? (int)(last.grid.x * last.grid.y) : 0;
     const CnCfg &fin = cn[dim == 3 ? 2 : 1];
-    if ((rc = dalloc(&partial, (size_t)fin.grid.x * fin.grid.y))) return rc;
+    // norm partials of the final pass (twice its default grid: a batch may run
+    // the pass with half-width tiles)
+    if ((rc = dalloc(&partial, 2 * (size_t)fin.grid.x * fin.grid.y))) return rc;
     if ((rc = dalloc(&obs_part, (size_t)obs_blocks * OBS_COUNT))) return rc;
     if ((rc = dalloc(&dip_part, (size_t)std::max(ndip, 1)))) return rc;
     if ((rc = dalloc(&obs_out, OBS_COUNT + 1))) return rc;
@@ -289,10 +363,11 @@ template <typename R> struct EngineT : Engine {
     const int n = (axis == 1) ? ny : nz;
     c.n = n;
     c.ncols = nx;
-    const int tpl = n / CMAX;
-    if (tpl < 1 || tpl > 32 || n % CMAX) { err = "line length not supported by the CN chunking"; return DGPE_EUNSUPPORTED; }
+    const int cl = variant_cl(var[axis]);
+    const int tpl = n / cl;
+    if (tpl < 1 || tpl > 32 || n % cl || !is_pow2(tpl)) { err = "line length not supported by the CN chunking"; return DGPE_EUNSUPPORTED; }
     c.TPL = tpl;
-    c.C = CMAX;
+    c.C = cl;
     c.W = std::min(W, DGPE_MAXT / tpl);  // blocks of at most DGPE_MAXT threads
     c.pitch = n + n / c.C + 1;
     c.T = c.W * tpl;
@@ -384,29 +459,57 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
 
+  // The opt-in dynamic shared-memory limit is a property of the kernel, shared
+  // by every solver that launches it, so it is raised to the device maximum
+  // (never set to one solver's size, which could be below another's).
   template <typename K> int smem_attr(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-      DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    int dev = 0, optin = 0;
+    DGPE_CK(cudaGetDevice(&dev));
+    DGPE_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    DGPE_CK(cudaFuncGetAttributes(&fa, kernel));
+    const size_t room = (size_t)optin - fa.sharedSizeBytes;
+    if (bytes > room) { err = "tile needs more shared memory than the device offers"; return DGPE_EUNSUPPORTED; }
+    DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room));
     DGPE_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     return DGPE_OK;
   }
   int set_smem_attrs() {
-    int rc;
-    if ((rc = smem_attr(k_dens_r2c_x<R, EPT_X>, x_smem))) return rc;
-    if ((rc = smem_attr(k_dens_r2c_x<R, EPT_X, 1>, x_smem))) return rc;
-    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 2>, x_smem))) return rc;
-    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0>, x_smem))) return rc;
-    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0>, x_smem))) return rc;
-    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1>, x_smem))) return rc;
-    if ((rc = smem_attr(k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 1>, x_smem))) return rc;
-    const size_t fs = std::max(fy.smem, fz.smem);
-    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 0>, fs))) return rc;
-    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 1>, fs))) return rc;
-    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 2>, fs))) return rc;
-    if ((rc = smem_attr(k_fft_strided<R, EPT_S, 3>, fs))) return rc;
-    const size_t cs = std::max(cn[1].smem, dim == 3 ? cn[2].smem : 0);
-    if ((rc = smem_attr(k_cn_strided<R, R, CMAX>, cs))) return rc;
-    if ((rc = smem_attr(k_cn_strided<R, Cx, CMAX>, cs))) return rc;
+    int rc = with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
+      constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
+      constexpr bool P2 = decltype(P2c)::value;
+      int r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2>, x_smem))) return r;
+      return DGPE_OK;
+    });
+    if (rc) return rc;
+    for (int a = 1; a < dim; ++a) {
+      const size_t fs = (a == 1) ? fy.smem : fz.smem;
+      rc = with_svar<EPT_S>(var[a], [&](auto EPc, auto P2c) -> int {
+        constexpr int EP = decltype(EPc)::value;
+        constexpr bool P2 = decltype(P2c)::value;
+        int r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 0, P2>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 1, P2>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 2, P2>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 3, P2>, fs))) return r;
+        return DGPE_OK;
+      });
+      if (rc) return rc;
+      rc = with_cl(var[a], [&](auto CLc) -> int {
+        constexpr int CL = decltype(CLc)::value;
+        int r;
+        if ((r = smem_attr(k_cn_strided<R, R, CL>, cn[a].smem))) return r;
+        if ((r = smem_attr(k_cn_strided<R, Cx, CL>, cn[a].smem))) return r;
+        return DGPE_OK;
+      });
+      if (rc) return rc;
+    }
     return DGPE_OK;
   }
 
@@ -428,13 +531,18 @@ template <typename R> struct EngineT : Engine {
   }
   int launch_fft(const FtCfg &f, int mode, cudaStream_t s) {
     SArgs<R> A = sargs(f);
-    switch (mode) {
-      case 0: k_fft_strided<R, EPT_S, 0><<<f.grid, f.T, f.smem, s>>>(A); break;
-      case 1: k_fft_strided<R, EPT_S, 1><<<f.grid, f.T, f.smem, s>>>(A); break;
-      case 2: k_fft_strided<R, EPT_S, 2><<<f.grid, f.T, f.smem, s>>>(A); break;
-      default: k_fft_strided<R, EPT_S, 3><<<f.grid, f.T, f.smem, s>>>(A); break;
-    }
-    DGPE_CK(cudaGetLastError());
+    with_svar<EPT_S>(var[f.axis], [&](auto EPc, auto P2c) -> int {
+      constexpr int EP = decltype(EPc)::value;
+      constexpr bool P2 = decltype(P2c)::value;
+      switch (mode) {
+        case 0: k_fft_strided<R, EP, 0, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
+        case 1: k_fft_strided<R, EP, 1, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
+        case 2: k_fft_strided<R, EP, 2, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
+        default: k_fft_strided<R, EP, 3, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
+      }
+      return DGPE_OK;
+    });
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   int launch_cn(int axis, bool final_pass, cudaStream_t s, Cx *buf = nullptr, bool adjoint = false) {
@@ -445,22 +553,28 @@ template <typename R> struct EngineT : Engine {
     A.step = dstep; A.estride = c.es; A.ostride = c.os; A.n = c.n; A.ncols = c.ncols; A.W = c.W;
     A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
     A.norm = (final_pass && imag) ? 1 : 0; A.tau = adjoint ? -tau[axis] : tau[axis];
-    if (imag) k_cn_strided<R, R, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
-    else k_cn_strided<R, Cx, CMAX><<<c.grid, c.T, c.smem, s>>>(A);
-    DGPE_CK(cudaGetLastError());
+    with_cl(var[axis], [&](auto CLc) -> int {
+      constexpr int CL = decltype(CLc)::value;
+      if (imag) k_cn_strided<R, R, CL><<<c.grid, c.T, c.smem, s>>>(A);
+      else k_cn_strided<R, Cx, CL><<<c.grid, c.T, c.smem, s>>>(A);
+      return DGPE_OK;
+    });
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   // density (of `src`, or the real field `dens_in`) -> half spectrum along x
   int launch_forward_spectrum(cudaStream_t s, const Cx *src = nullptr, const R *dens_in = nullptr) {
     XArgs<R> A = xargs();
     if (src) A.psi = const_cast<Cx *>(src);
-    if (dens_in) {
-      A.dens_in = dens_in;
-      k_dens_r2c_x<R, EPT_X, 1><<<x_grid, x_T, x_smem, s>>>(A);
-    } else {
-      k_dens_r2c_x<R, EPT_X><<<x_grid, x_T, x_smem, s>>>(A);
-    }
-    DGPE_CK(cudaGetLastError());
+    if (dens_in) A.dens_in = dens_in;
+    with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
+      constexpr int EX = decltype(EXc)::value;
+      constexpr bool P2 = decltype(P2c)::value;
+      if (dens_in) k_dens_r2c_x<R, EX, 1, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      else k_dens_r2c_x<R, EX, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      return DGPE_OK;
+    });
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   // mode 0: step pass on psi; 1: Phi_d into phi_out; 2: CN_x (conjugated) on buf
@@ -468,17 +582,24 @@ template <typename R> struct EngineT : Engine {
     XArgs<R> A = xargs();
     if (buf) A.psi = buf;
     if (phi_out) A.phi_out = phi_out;
-    if (mode == 0) {
-      if (imag) k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
-      else k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 0><<<x_grid, x_T, x_smem, s>>>(A);
-    } else if (mode == 1) {
-      k_c2r_x_exp_cnx<R, R, EPT_X, CMAX, 1><<<x_grid, x_T, x_smem, s>>>(A);
-    } else {
+    if (mode == 2) {
       A.cntab = cntab_adj[0];
       A.tau = -tau[0];
-      k_c2r_x_exp_cnx<R, Cx, EPT_X, CMAX, 2><<<x_grid, x_T, x_smem, s>>>(A);
     }
-    DGPE_CK(cudaGetLastError());
+    with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
+      constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
+      constexpr bool P2 = decltype(P2c)::value;
+      if (mode == 0) {
+        if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+        else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      } else if (mode == 1) {
+        k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      } else {
+        k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      }
+      return DGPE_OK;
+    });
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   // Phi_d chain up to (not including) the C2R along x.
@@ -621,7 +742,7 @@ template <typename R> struct EngineT : Engine {
     const int blocks = 152 * 8;
     if (fp64) k_import<R, double2><<<blocks, 256, 0, s>>>(psi, (const double2 *)src, nsites);
     else k_import<R, float2><<<blocks, 256, 0, s>>>(psi, (const float2 *)src, nsites);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     int rc = reset_scale(s);
     if (rc) return rc;
     return set_time(0, s);
@@ -630,28 +751,31 @@ template <typename R> struct EngineT : Engine {
     const int blocks = 152 * 8;
     if (fp64) k_export<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, psi, prm, nsites);
     else k_export<R, float2><<<blocks, 256, 0, s>>>((float2 *)dst, psi, prm, nsites);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   int observables(dgpe_obs *o, cudaStream_t s) override {
     int rc;
+    DGPE_LCK("(pending before observables)");
     if (has_dip) {
       if ((rc = launch_forward_spectrum(s))) return rc;
+      DGPE_LCK("density/R2C");
       if (dim == 3) {
         if ((rc = launch_fft(fy, 0, s))) return rc;
         if ((rc = launch_fft(fz, 3, s))) return rc;
       } else {
         if ((rc = launch_fft(fy, 3, s))) return rc;
       }
+      DGPE_LCK("spectral energy sum");
     }
     OArgs<R> A{};
     A.psi = psi; A.prm = prm; A.partial = obs_part; A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
     A.rows_per_block = 0; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
     A.nux = p.nu[0]; A.nuy = p.nu[1]; A.nuz = (dim == 3) ? p.nu[2] : 0.0;
     k_obs_sites<R><<<obs_blocks, 256, 0, s>>>(A);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK("site sums");
     k_obs_final<<<1, 256, 0, s>>>(obs_part, obs_blocks, dip_part, ndip, obs_out);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK("final sums");
     double h[OBS_COUNT + 1];
     double hp[PRM_COUNT];
     long long st = 0;
@@ -711,7 +835,7 @@ template <typename R> struct EngineT : Engine {
     if (mode != DGPE_IMAG && mode != DGPE_REAL) { err = "bad mode"; return DGPE_EINVAL; }
     // fold the lazy scale into psi, then rebuild the CN tables and the graph
     k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, nsites);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     int rc = reset_scale(s);
     if (rc) return rc;
     p.mode = mode;
@@ -768,7 +892,7 @@ template <typename R> struct EngineT : Engine {
     const int nblk = 152 * 8;
     k_adj_sigma<R><<<nblk, 256, 0, s>>>(A);
     k_adj_accumulate<<<1, 256, 0, s>>>(adj_part, nblk, adj_acc, p.dt, t, host_M);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     if (has_dip) {
       if ((rc = launch_dipolar_chain(s, nullptr, adj_sig))) return rc;
       if ((rc = launch_p1(1, s, nullptr, adj_ksig))) return rc;
@@ -776,7 +900,7 @@ template <typename R> struct EngineT : Engine {
       DGPE_CK(cudaMemsetAsync(adj_ksig, 0, sizeof(R) * nsites, s));
     }
     k_adj_update<R><<<nblk, 256, 0, s>>>(A);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     return DGPE_OK;
   }
   int step_adjoint(const void *psi_in, void *G, long long st, double *dg, double *dc,
@@ -818,7 +942,7 @@ template <typename R> struct EngineT : Engine {
     // c = h^d sum conj(target) psi_T, F = |c|^2, G_T = 2 h^d c target
     const int nblk = 152 * 8;
     k_cdot<R><<<nblk, 256, 0, s>>>(adjT, psi, nsites, adj_part);
-    DGPE_CK(cudaGetLastError());
+    DGPE_LCK(__func__);
     std::vector<double> part(2 * nblk);
     DGPE_CK(cudaMemcpyAsync(part.data(), adj_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
     DGPE_CK(cudaStreamSynchronize(s));
@@ -862,4 +986,5 @@ template <typename R> struct EngineT : Engine {
   }
 };
 
+}  // namespace
 }  // namespace dgpe

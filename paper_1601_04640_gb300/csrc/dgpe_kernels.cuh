@@ -14,7 +14,11 @@
 
 #include "dgpe_device.cuh"
 
+// Kernels have internal linkage (unnamed namespace): every translation unit
+// that launches a kernel registers and configures its own copy, so a kernel
+// attribute set in one unit always applies to the copy that unit launches.
 namespace dgpe {
+namespace {
 
 // FP64 parameter block read by every pass (so quenches and modulation need no
 // graph re-capture).  Index constants:
@@ -143,8 +147,8 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 #define DGPE_MAXT 256
 
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
-template <typename R, int EPT, int SRC = 0>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
+template <typename R, int EPT, int SRC, bool POW2>
+__device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
   constexpr int PW = Pad<R>::W;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
     return mk<R>(d0, d1);
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
-  tile_fft<R, EPT, false, false, PW>(zt, SL, 1, A.LP, A.pl, A.tw, load, store);
+  tile_fft<R, EPT, false, false, PW, POW2>(zt, SL, 1, A.LP, A.pl, A.tw, load, store);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
   const int nh = n / 2 + 1;
@@ -181,21 +185,39 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
     if (r1 < nrows) A.spec[(size_t)r1 * A.px + k] = X1;
   }
 }
+template <typename R, int EPT, int SRC = 0, bool POW2 = true>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
+  dens_r2c_x_body<R, EPT, SRC, POW2>(A);
+}
+// batched: one problem per blockIdx.z
+template <typename R, int EPT, bool POW2>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x_batch(const XArgs<R> *__restrict__ args) {
+  const XArgs<R> A = args[blockIdx.z];
+  if (blockIdx.x * A.LP * 2 >= (unsigned)A.nrows) return;
+  dens_r2c_x_body<R, EPT, 0, POW2>(A);
+}
 
 // ------------------------------------------------------------------ P1
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
 // MODE 2: CN_x alone (the reverse step applies it to the adjoint field).
-template <typename R, typename Coef, int EPT, int CL, int MODE>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2>
+__device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
   cx<R> *zt = pt + 2 * A.LP * A.pitch;           // Z tile: LP lines, pitch pitchz
   constexpr int PW = Pad<R>::W;
   __shared__ double s_dts;
+  __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
-  const int ln = ilog2(n), lny = ilog2(A.ny);
+  const int ln = POW2 ? ilog2(n) : 0;
   const int p0 = blockIdx.x * A.LP;
   const int T = blockDim.x, t = threadIdx.x;
+  auto row_of = [&](int idx) { return POW2 ? (idx >> ln) : (idx / n); };
+  auto col_of = [&](int idx) { return POW2 ? (idx & (n - 1)) : (idx % n); };
+  if (t < 2 * A.LP) {
+    const int row = 2 * p0 + t;
+    s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
+  }
   if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
     // every load of the tile is issued before any is used (2 LP n = CL T)
@@ -203,14 +225,14 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
       const int idx = t + i * T;
-      const int L = idx >> ln, a = idx & (n - 1);
+      const int L = row_of(idx), a = col_of(idx);
       const int row = 2 * p0 + L;
       buf[i] = (row < nrows) ? A.psi[(size_t)row * n + a] : czero<cx<R>>();
     }
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
       const int idx = t + i * T;
-      const int L = idx >> ln, a = idx & (n - 1);
+      const int L = row_of(idx), a = col_of(idx);
       pt[L * P + a + a / CL] = buf[i];
     }
   }
@@ -223,12 +245,10 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
   const int imag = A.imag;
   // exponential substep on the tile element (L, a) in place
   auto apply_e = [&](int L, int a, R phi) {
-    const int row = 2 * p0 + L;
     const int ia = L * P + a + a / CL;
     cx<R> v = cscale(pt[ia], sc);
     const R dens = v.x * v.x + v.y * v.y;
-    const int y = row & (A.ny - 1), z = row >> lny;
-    const R V = A.vx[a] + A.vy[y] + A.vz[z];
+    const R V = A.vx[a] + s_vyz[L];
     const R th = dts * V + gdt * dens + gdddt * phi;
     pt[ia] = nonlinear_factor<R>(v, th, imag);
   };
@@ -255,9 +275,9 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
       apply_e(2 * l, a, v.x);
       apply_e(2 * l + 1, a, v.y);
     };
-    tile_fft<R, EPT, true, false, PW>(zt, A.pitchz, 1, A.LP, A.pl, A.tw, load, store);
+    tile_fft<R, EPT, true, false, PW, POW2>(zt, A.pitchz, 1, A.LP, A.pl, A.tw, load, store);
   } else if (MODE == 0) {
-    for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(idx >> ln, idx & (n - 1), (R)0);
+    for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
   }
   if (MODE == 1) return;
@@ -270,17 +290,26 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
     const int idx = t + i * T;
-    const int L = idx >> ln, a = idx & (n - 1);
+    const int L = row_of(idx), a = col_of(idx);
     const int row = 2 * p0 + L;
     if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
   }
+}
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
+  c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2>(A);
+}
+template <typename R, typename Coef, int EPT, int CL, bool POW2>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
+  const XArgs<R> A = args[blockIdx.z];
+  c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
 }
 
 // ------------------------------------------------- P5 / P6 / P7 (strided)
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
-template <typename R, int EPT, int MODE>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
+template <typename R, int EPT, int MODE, bool POW2>
+__device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
   __shared__ double red[32];
@@ -296,17 +325,17 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
     if (c0 + l < A.ncols) spec[base + a * es + l] = v;
   };
   if (MODE == 0) {
-    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
   } else if (MODE == 1) {
-    tile_fft<R, EPT, true, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
   } else if (MODE == 2) {
     auto mstore = [&](int l, int a, cx<R> v) {
       const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
       sm[a * W + l] = cscale(v, u);
     };
-    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, mstore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, mstore);
     auto sload = [&](int l, int a) -> cx<R> { return sm[a * W + l]; };
-    tile_fft<R, EPT, true, true, 0>(sm, 1, W, W, A.pl, A.tw, sload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, sload, gstore);
   } else {
     double acc = 0.0;
     auto astore = [&](int l, int a, cx<R> v) {
@@ -316,15 +345,24 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
         acc += w * (double)A.U[base + a * es + l] * ((double)v.x * v.x + (double)v.y * v.y);
       }
     };
-    tile_fft<R, EPT, false, true, 0>(sm, 1, W, W, A.pl, A.tw, gload, astore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, astore);
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
+template <typename R, int EPT, int MODE, bool POW2 = true>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
+  fft_strided_body<R, EPT, MODE, POW2>(A);
+}
+template <typename R, int EPT, int MODE, bool POW2>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
+  const SArgs<R> A = args[blockIdx.z];
+  fft_strided_body<R, EPT, MODE, POW2>(A);
+}
 
 // ------------------------------------------------------- P2 / P3 (strided)
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided(CArgs<R> A) {
+__device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *tile = reinterpret_cast<cx<R> *>(smraw);  // [W][pitch]
   __shared__ double red[32];
@@ -396,6 +434,15 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided(CArgs<R> A) {
     *A.step += 1;
     *A.counter = 0u;
   }
+}
+template <typename R, typename Coef, int CL>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided(CArgs<R> A) {
+  cn_strided_body<R, Coef, CL>(A);
+}
+template <typename R, typename Coef, int CL>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
+  const CArgs<R> A = args[blockIdx.z];
+  cn_strided_body<R, Coef, CL>(A);
 }
 
 // ------------------------------------------------------------ observables
@@ -598,4 +645,5 @@ __global__ void k_fold_scale(cx<R> *psi, double *prm, size_t n) {
     psi[i] = cscale(psi[i], sc);
 }
 
+}  // namespace
 }  // namespace dgpe

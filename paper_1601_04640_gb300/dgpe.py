@@ -42,6 +42,9 @@ EXPORTS = [
     "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes",
     "dgpe_dipolar_potential_noalloc", "dgpe_noalloc_last_error",
     "dgpe_step_adjoint", "dgpe_fidelity_gradient",
+    "dgpe_batch_create", "dgpe_batch_destroy", "dgpe_batch_set_psi", "dgpe_batch_get_psi",
+    "dgpe_batch_step", "dgpe_batch_observables", "dgpe_batch_info", "dgpe_batch_launches_per_step",
+    "dgpe_batch_last_error",
 ]
 
 
@@ -344,3 +347,76 @@ def dgpe_fidelity_gradient(h, psi0, target, nsteps: int, every: int, M: int = 0)
     _check(lib.dgpe_fidelity_gradient(h, a.ctypes.data, b.ctypes.data, int(nsteps), int(every),
                                       C.byref(F), C.byref(dg), dc), h)
     return F.value, dg.value, [dc[i] for i in range(M)]
+
+
+# ------------------------------------------------------------- batched form
+class Batch:
+    """Many independent 2D XY problems (FP32-bulk) stepped by one graph launch.
+
+    problems: list of dicts with keys n (nx, ny), h, nu, g, gdd, dt, imag, qd."""
+
+    def __init__(self, problems, stream: int = 0):
+        lib = load()
+        if not getattr(lib, "_batch_bound", False):
+            lib.dgpe_batch_create.argtypes = [C.POINTER(dgpe_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+            lib.dgpe_batch_destroy.argtypes = [C.c_void_p]
+            lib.dgpe_batch_destroy.restype = None
+            lib.dgpe_batch_set_psi.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
+            lib.dgpe_batch_get_psi.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
+            lib.dgpe_batch_step.argtypes = [C.c_void_p, C.c_int]
+            lib.dgpe_batch_observables.argtypes = [C.c_void_p, C.c_int, C.POINTER(dgpe_obs)]
+            lib.dgpe_batch_info.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                            C.POINTER(C.c_double)]
+            lib.dgpe_batch_launches_per_step.argtypes = [C.c_void_p]
+            lib.dgpe_batch_last_error.argtypes = [C.c_void_p]
+            lib.dgpe_batch_last_error.restype = C.c_char_p
+            lib._batch_bound = True
+        self.lib = lib
+        arr = (dgpe_params * len(problems))()
+        self.shapes = []
+        for i, q in enumerate(problems):
+            arr[i] = make_params(2, q["n"], q["h"], q["nu"], q["g"], q["gdd"], q["dt"], q["imag"], False,
+                                 DGPE_KERNEL_QUASI2D_XY, q.get("qd", 0.5))
+            self.shapes.append((q["n"][1], q["n"][0]))
+        self.h = C.c_void_p()
+        rc = lib.dgpe_batch_create(arr, len(problems), C.c_void_p(stream), C.byref(self.h))
+        if rc:
+            raise DgpeError(rc, lib.dgpe_batch_last_error(None).decode())
+
+    def _chk(self, rc):
+        if rc:
+            raise DgpeError(rc, self.lib.dgpe_batch_last_error(self.h).decode())
+
+    def set_psi(self, i, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        self._chk(self.lib.dgpe_batch_set_psi(self.h, i, a.ctypes.data, a.size))
+
+    def get_psi(self, i):
+        out = np.empty(self.shapes[i], dtype=np.complex128)
+        self._chk(self.lib.dgpe_batch_get_psi(self.h, i, out.ctypes.data, out.size))
+        return out
+
+    def step(self, n=1):
+        self._chk(self.lib.dgpe_batch_step(self.h, int(n)))
+
+    def observables(self, i):
+        o = dgpe_obs()
+        self._chk(self.lib.dgpe_batch_observables(self.h, i, C.byref(o)))
+        return {"norm": o.norm, "mu": o.mu, "energy": o.energy, "rms": (o.rms[0], o.rms[1], o.rms[2])}
+
+    def info(self):
+        c, s, b = C.c_int(), C.c_longlong(), C.c_double()
+        self._chk(self.lib.dgpe_batch_info(self.h, C.byref(c), C.byref(s), C.byref(b)))
+        return {"classes": c.value, "sites": s.value, "bytes_per_step": b.value,
+                "launches_per_step": self.lib.dgpe_batch_launches_per_step(self.h)}
+
+    def close(self):
+        if self.h:
+            self.lib.dgpe_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

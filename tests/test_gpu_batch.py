@@ -1,0 +1,56 @@
+"""Batched 2D form: every problem of a mixed-size, mixed-mode sweep against the
+same problem run alone (bit-identical: same kernels, same arithmetic per line)
+and against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_04640_gb300 import build as gbuild
+from paper_1601_04640_gb300 import dgpe, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _psi0(q):
+    nu = (1.0, q["nu"][1])
+    return synth.gaussian_state(q["n"], q["h"], nu, 0.01, q["seed"])
+
+
+def test_batch_matches_single_and_oracle():
+    gbuild.build()
+    probs = synth.batched_problems(4640, 10, sizes=synth.BATCH_SIZES)
+    # make sure every size and both modes appear
+    for i, n in enumerate(synth.BATCH_SIZES):
+        probs[i]["n"] = (n, n)
+    steps = 20
+    with dgpe.Batch(probs) as B:
+        info = B.info()
+        assert info["sites"] == sum(q["n"][0] * q["n"][1] for q in probs)
+        for i, q in enumerate(probs):
+            B.set_psi(i, _psi0(q))
+        B.step(steps)
+        outs = [B.get_psi(i) for i in range(len(probs))]
+        obs = [B.observables(i) for i in range(len(probs))]
+    for i, q in enumerate(probs):
+        psi0 = _psi0(q)
+        with dgpe.Solver(2, q["n"], q["h"], q["nu"], q["g"], q["gdd"], q["dt"], q["imag"], False,
+                         qd=q["qd"]) as s:
+            s.set_psi(psi0)
+            s.step(steps)
+            single = s.get_psi()
+        assert np.array_equal(outs[i], single), i
+        op = oracle.Params(dim=2, n=q["n"], h=q["h"], nu=q["nu"], g=q["g"], gdd=q["gdd"], dt=q["dt"],
+                           imag=q["imag"], kernel="quasi2d", qd=q["qd"])
+        ref = oracle.step(op, psi0, 0, steps)
+        e = np.linalg.norm(outs[i] - ref) / np.linalg.norm(ref)
+        r = oracle.observables(op, ref, steps)
+        print(i, q["n"], "imag" if q["imag"] else "real", "rel L2", e, "mu", obs[i]["mu"], r["mu"])
+        assert e < 1e-5
+        assert abs(obs[i]["mu"] - r["mu"]) <= 1e-6 * abs(r["mu"])
+
+
+def test_batch_rejects_bad_problems():
+    gbuild.build()
+    q = dict(n=(64, 32), h=(0.2, 0.2), nu=(1.0, 1.0), g=10.0, gdd=1.0, dt=1e-3, imag=True, qd=0.5)
+    with pytest.raises(dgpe.DgpeError):
+        dgpe.Batch([q])

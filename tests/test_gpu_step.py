@@ -48,6 +48,7 @@ def gpu_run(dim, n, h, nu, g, gdd, dt, imag, fp64, kc, psi0, steps, graph=True):
 CASES_3D = [
     ((32, 32, 32), (0.25, 0.25, 0.25), (1.0, 1.0, 2.0)),
     ((64, 32, 128), (0.2, 0.3, 0.1), (1.0, 1.3, 0.8)),
+    ((96, 160, 48), (0.2, 0.15, 0.3), (1.0, 1.2, 1.5)),   # 3 * 2^k and 5 * 2^k lengths
 ]
 
 
@@ -94,8 +95,9 @@ def test_step_parity_3d(fp64, imag, case):
 
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("imag", [True, False])
-def test_step_parity_2d(fp64, imag):
-    n, h, nu = (64, 32), (0.2, 0.3), (1.0, 1.5)
+@pytest.mark.parametrize("n", [(64, 32), (96, 160), (384, 80), (512, 64)])
+def test_step_parity_2d(fp64, imag, n):
+    h, nu = (0.2, 0.3), (1.0, 1.5)
     op, kc, psi0 = make_case(2, n, h, nu, 80.0, 40.0, 1e-3, imag)
     psi, obs = gpu_run(2, n, h, nu, 80.0, 40.0, 1e-3, imag, fp64, kc, psi0, 10)
     ref = oracle.step(op, psi0, 0, 10)
