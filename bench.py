@@ -36,6 +36,15 @@ WORKLOADS = {
                   gdd=200.0, dt=2e-4, widths=(1.0, 1.0, 3.0), seed=2016, prep_steps=0,
                   desc="large real3d 512x512x256, h=0.08, pancake nu=(1,1,3), g=500, g_dd=200, "
                        "dt=2e-4, from a seeded Gaussian"),
+    "batched2d": dict(n=None, desc="batched 2D: 512 independent XY problems, square grids from "
+                      "{64,96,128,160,256,384,512}^2, h=0.2, nu_y in [0.5,2], g in [10,200], g_dd/g in "
+                      "[0,0.8], quasi-2D kernel d=0.5, half imaginary / half real time, dt=1e-3, "
+                      "FP32-bulk, one graph launch per step (seed 4640)"),
+    "adjoint": dict(n=(128, 128, 128), h=(0.15, 0.15, 0.15), nu=(1.0, 1.0, 0.5), g=200.0, gdd=60.0,
+                    dt=1e-3, widths=(1.0, 1.0, 0.5), seed=160104640, g_prep=None, prep_steps=0,
+                    desc="adjoint real3d 128^3, h=0.15, FP32-bulk, dt=1e-3, 1000 steps, V(t)=V0(1+sum "
+                         "c_m sin(m t)), c_m~U(-0.05,0.05); fidelity gradient w.r.t. c_1..c_8 and g, "
+                         "checkpoint every 32 steps"),
     "imag3d": dict(n=(32, 32, 32), h=(0.25, 0.25, 0.25), nu=(1.0, 1.0, 2.0), g_prep=None, g=50.0,
                    gdd=15.0, dt=2e-3, widths=(1.0, 1.0, 2.0), seed=1601, prep_steps=0, imag=True,
                    desc="imag3d 32^3, h=0.25, nu=(1,1,2), g=50, g_dd=15, imaginary dt=0.002"),
@@ -167,11 +176,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     n = wl["n"]
-    sites = n[0] * n[1] * n[2]
+    sites = n[0] * n[1] * n[2] if n else 0
     metric = "3D split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline"
 
     if args.impl == "reference":
         if rank != 0:
+            return
+        if args.workload in ("batched2d", "adjoint"):
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm times the 3D step workloads only"}))
             return
         import oracle.build
         oracle.build.build()
@@ -192,6 +204,10 @@ def main():
     import torch
     from paper_1601_04640_gb300 import build as gbuild
     from paper_1601_04640_gb300 import dgpe, synth
+    if args.workload == "batched2d":
+        return bench_batched(args, wl, world, rank, local)
+    if args.workload == "adjoint":
+        return bench_adjoint(args, wl, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -353,6 +369,145 @@ def main():
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _peak_line(metric, value, unit, steps, warmup, ms, dtype, cfg, world, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg}
+    line.update(extra)
+    return line
+
+
+def bench_batched(args, wl, world, rank, local):
+    """512 independent 2D problems stepped by one graph launch per step."""
+    import torch
+    from paper_1601_04640_gb300 import build as gbuild
+    from paper_1601_04640_gb300 import dgpe, synth
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    gbuild.build()
+    stream = torch.cuda.Stream()
+    probs = synth.batched_problems(4640 + rank, 512)
+    hbm_peak, peak_kind = peaks()
+    states = []
+    for q in probs:
+        noise = 0.01 if q["imag"] else 0.0
+        states.append(synth.gaussian_state(q["n"], q["h"], (1.0, q["nu"][1]), noise, q["seed"]))
+    t0 = time.perf_counter()
+    B = dgpe.Batch(probs, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    info = B.info()
+    for i, st in enumerate(states):
+        B.set_psi(i, st)
+    B.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    sites = info["sites"]
+    per_step = ms / args.steps
+    gbs = info["bytes_per_step"] / (per_step * 1e-3) / 1e9
+    sizes = {}
+    for q in probs:
+        sizes[q["n"][0]] = sizes.get(q["n"][0], 0) + 1
+    # end to end: every step copies all 512 states in from the host and back
+    ke = 2
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        for i, st in enumerate(states):
+            B.set_psi(i, st)
+        B.step(1)
+        outs = [B.get_psi(i) for i in range(len(probs))]
+    te = time.perf_counter() - t0
+    obs0 = B.observables(0)
+    B.close()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        import oracle.build
+        oracle.build.build()
+        t0, done, steps = time.perf_counter(), 0, 0
+        for i, q in enumerate(probs[:64]):
+            op = oracle.Params(dim=2, n=q["n"], h=q["h"], nu=q["nu"], g=q["g"], gdd=q["gdd"], dt=q["dt"],
+                               imag=q["imag"], kernel="quasi2d", qd=q["qd"])
+            oracle.step(op, states[i], 0, 2)
+            done += 2 * q["n"][0] * q["n"][1]
+            if time.perf_counter() - t0 > 15:
+                break
+        dtc = time.perf_counter() - t0
+        cpu = {"value": done / dtc, "unit": "site-updates/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": "2 steps of each of the first %d problems of the sweep" % (i + 1)}
+    line = _peak_line("2D batched split-step site-updates/s and % of HBM roofline",
+                      world * sites * args.steps / (ms * 1e-3), "site-updates/s", args.steps, args.warmup,
+                      per_step, "f32 (FP64 reductions/tables)",
+                      {"workload": wl["desc"], "problems": len(probs), "sites": sites, "sizes": sizes,
+                       "classes": info["classes"], "l2": "inputs larger than L2 (%d MB of state)" % (8 * sites >> 20),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                      world,
+                      roofline={"bound": "hbm", "kernel": "whole batched step", "achieved": gbs,
+                                "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+                                "traffic": None, "algorithmic_bytes_per_step": info["bytes_per_step"]},
+                      e2e={"value": sites * ke / te, "unit": "site-updates/s", "h2d_bytes_per_step": 16 * sites,
+                           "d2h_bytes_per_step": 16 * sites},
+                      gpu_launches=info["launches_per_step"] * args.steps, clocks=clocks, cpu_baseline=cpu,
+                      create_s=t_create, observables_problem0={"mu": obs0["mu"], "norm": obs0["norm"]})
+    print(json.dumps(line))
+
+
+def bench_adjoint(args, wl, world, rank, local):
+    """One fidelity + gradient evaluation (forward with checkpoints, reverse sweep)."""
+    import torch
+    from paper_1601_04640_gb300 import build as gbuild
+    from paper_1601_04640_gb300 import dgpe, synth
+    torch.cuda.set_device(local)
+    gbuild.build()
+    n, h = wl["n"], wl["h"]
+    cm = list(synth.trap_modulation(wl["seed"], 8, 0.05))
+    psi0 = synth.gaussian_state(n, h, wl["widths"], 0.01, 1)
+    target = synth.gaussian_state(n, h, (1.1, 0.9, 0.5), 0.01, 2)
+    K = args.steps if args.steps > 20 else 1000
+    every = 32
+    out = {}
+    for fp64 in (False, True):
+        if fp64 and K > 200:
+            Kf = 200
+        else:
+            Kf = K
+        with dgpe.Solver(3, n, h, wl["nu"], wl["g"], wl["gdd"], wl["dt"], False, fp64) as s:
+            s.set_trap_modulation(cm)
+            dgpe.dgpe_fidelity_gradient(s.h, psi0, target, 2 * every, every, len(cm))  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F, dg, dc = dgpe.dgpe_fidelity_gradient(s.h, psi0, target, Kf, every, len(cm))
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        sites = n[0] * n[1] * n[2]
+        out["fp64" if fp64 else "fp32_bulk"] = {"steps": Kf, "seconds": dt, "value": sites * Kf / dt,
+                                                 "F": F, "dF_dg": dg, "dF_dc": dc}
+    a = out["fp32_bulk"]
+    line = _peak_line("adjoint: forward+reverse site-updates/s of one fidelity gradient", a["value"],
+                      "site-updates/s", a["steps"], 1, 1e3 * a["seconds"] / a["steps"],
+                      "f32 (FP64 reductions/tables)", {"workload": wl["desc"], "grid": list(n)}, 1,
+                      forms=out, gpu_launches=None)
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

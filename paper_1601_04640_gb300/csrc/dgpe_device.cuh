@@ -336,10 +336,11 @@ __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &p
 // a Kogge-Stone scan of the chunk maps (P, Y) over the lanes, and a fix-up
 // with the in-chunk products P_a = prod_{b=a0..a} alpha_b and
 // Q_a = prod_{b=a..a0+CL-1} alpha_b.  With TABLES the kernel reads m, alpha,
-// P, Q (n each, in that order); without, it reads m and forms alpha, P, Q in
-// registers (cheaper where arithmetic is plentiful).  The line lives in shared
-// memory at line[a + a / CL] (one pad per chunk keeps the lanes' accesses on
-// distinct banks).
+// P, Q (n each, in that order) from global memory; without, `tab` is a shared
+// copy of m in the padded layout below, and alpha, P, Q are formed in
+// registers (cheaper where arithmetic is plentiful).  The line lives in
+// shared memory at line[a + a / CL] (one pad per chunk keeps the lanes'
+// accesses on distinct banks).
 template <typename R, typename Coef, int CL, bool TABLES>
 __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef kt,
                                         const Coef *__restrict__ tab, bool active) {
@@ -359,7 +360,7 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef
     Cx nxt = (active && a + 1 < n) ? line[(a + 1) + (a + 1) / CL] : czero<Cx>();
     Cx lap = cur + cur - prev - nxt;
     Cx r = coef_mul(m2kt, lap);
-    const Coef ma = active ? tm[a] : coef_zero<Coef>();
+    const Coef ma = active ? (TABLES ? tm[a] : tm[a + a / CL]) : coef_zero<Coef>();
     Coef al;
     if (TABLES) {
       al = active ? ta[a] : coef_zero<Coef>();
@@ -424,6 +425,30 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef
       line[ia] = line[ia] + w;
     }
   }
+}
+
+// Copy the m table of an axis (n coefficients) into shared memory in the
+// padded layout cn_line reads (index a + a / CL).  All threads take part.
+template <typename Coef, int CL>
+__device__ __forceinline__ void stage_m_table(Coef *dst, const Coef *__restrict__ m, int n) {
+  for (int a = threadIdx.x; a < n; a += blockDim.x) dst[a + a / CL] = m[a];
+}
+
+// ------------------------------------------------ asynchronous tile copies
+// cp.async global -> shared copies (issued by every thread for its own
+// elements, completed per commit group) let a persistent CTA fetch its next
+// tile while it computes the current one.
+__device__ __forceinline__ void cp_async_elem(float2 *smem, const float2 *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2 *smem, const double2 *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // --------------------------------------------------- FP64 block reductions

@@ -78,7 +78,8 @@ inline bool make_plan(int n, int ept, FftPlan &pl) {
 //   powers of two: CL 16, EPT_X 8, EPT_S 8 (FP64) / 16 (FP32)
 //   3 * 2^k:       CL 12, EPT_X 12, EPT_S 12  (radices 4, 3, 2)
 //   5 * 2^k:       CL 10, EPT_X 20, EPT_S 20  (radices 5, 4, 2)
-enum { VAR_P2 = 0, VAR_3 = 1, VAR_5 = 2, VAR_NONE = -1 };
+//   (VAR_P2S: CL 8 for short power-of-two lines; measured slower, unused)
+enum { VAR_P2 = 0, VAR_3 = 1, VAR_5 = 2, VAR_P2S = 3, VAR_NONE = -1 };
 inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 inline int axis_variant(int n) {
   if (is_pow2(n) && n >= 32 && n <= 512) return VAR_P2;
@@ -86,12 +87,13 @@ inline int axis_variant(int n) {
   if (n % 5 == 0 && is_pow2(n / 5) && n % 10 == 0 && n / 10 <= 32) return VAR_5;
   return VAR_NONE;
 }
-inline int variant_cl(int v) { return v == VAR_P2 ? 16 : v == VAR_3 ? 12 : 10; }
+inline int variant_cl(int v) { return v == VAR_P2 ? 16 : v == VAR_P2S ? 8 : v == VAR_3 ? 12 : 10; }
 
 // Call f(CL, EPT_X, POW2) with compile-time constants for variant v.
 template <class F> int with_xvar(int v, F &&f) {
   switch (v) {
     case VAR_P2: return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 8>{}, std::true_type{});
+    case VAR_P2S: return f(std::integral_constant<int, 8>{}, std::integral_constant<int, 8>{}, std::true_type{});
     case VAR_3: return f(std::integral_constant<int, 12>{}, std::integral_constant<int, 12>{}, std::false_type{});
     default: return f(std::integral_constant<int, 10>{}, std::integral_constant<int, 20>{}, std::false_type{});
   }
@@ -99,7 +101,8 @@ template <class F> int with_xvar(int v, F &&f) {
 // Call f(EPT_S, POW2) for the strided FFT of variant v (pow2 EPT_S given).
 template <int EPTP2, class F> int with_svar(int v, F &&f) {
   switch (v) {
-    case VAR_P2: return f(std::integral_constant<int, EPTP2>{}, std::true_type{});
+    case VAR_P2:
+    case VAR_P2S: return f(std::integral_constant<int, EPTP2>{}, std::true_type{});
     case VAR_3: return f(std::integral_constant<int, 12>{}, std::false_type{});
     default: return f(std::integral_constant<int, 20>{}, std::false_type{});
   }
@@ -108,12 +111,13 @@ template <int EPTP2, class F> int with_svar(int v, F &&f) {
 template <class F> int with_cl(int v, F &&f) {
   switch (v) {
     case VAR_P2: return f(std::integral_constant<int, 16>{});
+    case VAR_P2S: return f(std::integral_constant<int, 8>{});
     case VAR_3: return f(std::integral_constant<int, 12>{});
     default: return f(std::integral_constant<int, 10>{});
   }
 }
-inline int variant_ept_x(int v) { return v == VAR_P2 ? 8 : v == VAR_3 ? 12 : 20; }
-inline int variant_ept_s(int v, int p2) { return v == VAR_P2 ? p2 : v == VAR_3 ? 12 : 20; }
+inline int variant_ept_x(int v) { return (v == VAR_P2 || v == VAR_P2S) ? 8 : v == VAR_3 ? 12 : 20; }
+inline int variant_ept_s(int v, int p2) { return (v == VAR_P2 || v == VAR_P2S) ? p2 : v == VAR_3 ? 12 : 20; }
 
 // erfcx(u) = exp(u^2) erfc(u) for u >= 0; continued asymptotic series where
 // erfc underflows.
@@ -187,7 +191,14 @@ template <typename R> struct EngineT : Engine {
   // pass configurations
   int x_LP = 0, x_T = 0, x_TPL = 0, x_C = 0, x_pitchz = 0, x_pitch = 0, x_grid = 0;
   size_t x_smem = 0;
-  struct CnCfg { int n, ncols, W, TPL, C, pitch, T; long long es, os; dim3 grid; size_t smem; };
+  struct CnCfg {
+    int n, ncols, W, TPL, C, pitch, T;
+    long long es, os;
+    dim3 grid;
+    size_t smem;
+    int pgrid[2];  // persistent grid of the double-buffered kernel (real, complex coefficients)
+  };
+  int nsm = 1;
   CnCfg cn[3];   // index = axis (0 unused: x is fused into P1)
   struct FtCfg { int n, T, W; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
   FtCfg fy{}, fz{};
@@ -475,6 +486,11 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
   int set_smem_attrs() {
+    {
+      int dev = 0;
+      DGPE_CK(cudaGetDevice(&dev));
+      DGPE_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     int rc = with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
@@ -506,6 +522,15 @@ template <typename R> struct EngineT : Engine {
         int r;
         if ((r = smem_attr(k_cn_strided<R, R, CL>, cn[a].smem))) return r;
         if ((r = smem_attr(k_cn_strided<R, Cx, CL>, cn[a].smem))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, R, CL>, 2 * cn[a].smem))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL>, 2 * cn[a].smem))) return r;
+        // persistent grid: as many CTAs as fit on the device, at most one per tile
+        const int ntiles = (int)(cn[a].grid.x * cn[a].grid.y);
+        int occ = 0;
+        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, R, CL>, cn[a].T, 2 * cn[a].smem));
+        cn[a].pgrid[0] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
+        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, Cx, CL>, cn[a].T, 2 * cn[a].smem));
+        cn[a].pgrid[1] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
         return DGPE_OK;
       });
       if (rc) return rc;
@@ -553,10 +578,11 @@ template <typename R> struct EngineT : Engine {
     A.step = dstep; A.estride = c.es; A.ostride = c.os; A.n = c.n; A.ncols = c.ncols; A.W = c.W;
     A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
     A.norm = (final_pass && imag) ? 1 : 0; A.tau = adjoint ? -tau[axis] : tau[axis];
+    const int ncb = (int)c.grid.x, ntiles = (int)(c.grid.x * c.grid.y);
     with_cl(var[axis], [&](auto CLc) -> int {
       constexpr int CL = decltype(CLc)::value;
-      if (imag) k_cn_strided<R, R, CL><<<c.grid, c.T, c.smem, s>>>(A);
-      else k_cn_strided<R, Cx, CL><<<c.grid, c.T, c.smem, s>>>(A);
+      if (imag) k_cn_strided_pipe<R, R, CL><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+      else k_cn_strided_pipe<R, Cx, CL><<<c.pgrid[1], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
       return DGPE_OK;
     });
     DGPE_LCK(__func__);

@@ -143,8 +143,12 @@ __device__ __forceinline__ double trap_dts(const double *prm, long long step) {
 // elements per 128 bytes: the pad period of line-major tiles
 template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx<R>); };
 
-// Every pass is launched with at most DGPE_MAXT threads per block.
+// Every pass is launched with at most DGPE_MAXT threads per block and held to
+// 2 resident blocks per SM worth of registers (128 per thread); the FP32
+// strided transforms to 3 (about 85), which measured faster for them.
 #define DGPE_MAXT 256
+#define DGPE_MINB(R) 2
+#define DGPE_MINB_FFT(R) (sizeof(R) == 4 ? 3 : 2)
 
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
 template <typename R, int EPT, int SRC, bool POW2>
@@ -186,12 +190,12 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
   }
 }
 template <typename R, int EPT, int SRC = 0, bool POW2 = true>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_dens_r2c_x(XArgs<R> A) {
   dens_r2c_x_body<R, EPT, SRC, POW2>(A);
 }
 // batched: one problem per blockIdx.z
 template <typename R, int EPT, bool POW2>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_dens_r2c_x_batch(const XArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_dens_r2c_x_batch(const XArgs<R> *__restrict__ args) {
   const XArgs<R> A = args[blockIdx.z];
   if (blockIdx.x * A.LP * 2 >= (unsigned)A.nrows) return;
   dens_r2c_x_body<R, EPT, 0, POW2>(A);
@@ -208,6 +212,10 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   constexpr int PW = Pad<R>::W;
   __shared__ double s_dts;
   __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
+  constexpr bool TAB = (sizeof(R) == 8);
+  // FP32: shared copy of the m table (the CN solve forms the rest in registers)
+  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
+  if (!TAB && MODE != 1) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), A.nx);
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
   const int ln = POW2 ? ilog2(n) : 0;
   const int p0 = blockIdx.x * A.LP;
@@ -284,8 +292,8 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // Crank-Nicolson along x: TPL lanes per line
   const int l = t / A.TPL, q = t - l * A.TPL;
   const bool active = (2 * p0 + l) < nrows;
-  cn_line<R, Coef, CL, (sizeof(R) == 8)>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
-                                         reinterpret_cast<const Coef *>(A.cntab), active);
+  cn_line<R, Coef, CL, TAB>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                            TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, active);
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
@@ -296,11 +304,11 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   }
 }
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_c2r_x_exp_cnx(XArgs<R> A) {
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2>(A);
 }
 template <typename R, typename Coef, int EPT, int CL, bool POW2>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
   const XArgs<R> A = args[blockIdx.z];
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
 }
@@ -351,11 +359,11 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   }
 }
 template <typename R, int EPT, int MODE, bool POW2 = true>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided(SArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_FFT(R)) k_fft_strided(SArgs<R> A) {
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
 template <typename R, int EPT, int MODE, bool POW2>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_FFT(R)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
   const SArgs<R> A = args[blockIdx.z];
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
@@ -388,9 +396,15 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
     }
   }
   __syncthreads();
+  constexpr bool TAB = (sizeof(R) == 8);
+  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
+  if (!TAB) {
+    stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), n);
+    __syncthreads();
+  }
   const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-  cn_line<R, Coef, CL, (sizeof(R) == 8)>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
-                                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
+  cn_line<R, Coef, CL, TAB>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                            TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, c0 + l < A.ncols);
   __syncthreads();
   double acc = 0.0;
   if (c0 + lc < A.ncols) {
@@ -436,13 +450,102 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   }
 }
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided(CArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided(CArgs<R> A) {
   cn_strided_body<R, Coef, CL>(A);
 }
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, 2) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
   const CArgs<R> A = args[blockIdx.z];
   cn_strided_body<R, Coef, CL>(A);
+}
+
+// Persistent, double-buffered CN pass: each CTA walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the copies of the next tile into
+// the other shared buffer are in flight while the current tile is solved.
+// Tile id -> (column block id % nx_blocks, outer index id / nx_blocks).
+template <typename R, typename Coef, int CL>
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_pipe(CArgs<R> A, int ncb, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  __shared__ int am_last;
+  const int W = A.W, n = A.n, P = A.pitch;
+  const int lW = ilog2(W);
+  cx<R> *buf[2] = {reinterpret_cast<cx<R> *>(smraw), reinterpret_cast<cx<R> *>(smraw) + W * P};
+  const long long es = A.estride;
+  const int lc = threadIdx.x & (W - 1), r0 = threadIdx.x >> lW;
+  auto fetch = [&](int tile, cx<R> *tb) {
+    const int cb = tile % ncb, o = tile / ncb;
+    const int c0 = cb * W;
+    if (c0 + lc < A.ncols) {
+      const cx<R> *src = A.psi + (size_t)o * A.ostride + c0 + lc;
+#pragma unroll
+      for (int i = 0; i < CL; ++i) {
+        const int a = r0 + i * A.TPL;
+        cp_async_elem(tb + lc * P + a + a / CL, src + (size_t)a * es);
+      }
+    }
+    cp_async_commit();
+  };
+  constexpr bool TAB = (sizeof(R) == 8);
+  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
+  if (!TAB) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), n);  // visible after the loop's first barrier
+  double acc = 0.0;
+  int k = 0;
+  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, buf[0]);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) fetch(next, buf[k ^ 1]);
+    else cp_async_commit();  // keep one group per iteration
+    cp_async_wait<1>();      // this tile's copies are done (the next may be in flight)
+    __syncthreads();
+    const int cb = tile % ncb, o = tile / ncb;
+    const int c0 = cb * W;
+    cx<R> *tb = buf[k];
+    const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
+    cn_line<R, Coef, CL, TAB>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                              TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, c0 + l < A.ncols);
+    __syncthreads();
+    if (c0 + lc < A.ncols) {
+      cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;
+#pragma unroll
+      for (int i = 0; i < CL; ++i) {
+        const int a = r0 + i * A.TPL;
+        const cx<R> v = tb[lc * P + a + a / CL];
+        dst[(size_t)a * es] = v;
+        if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y;
+      }
+    }
+    __syncthreads();  // the buffer is refilled two iterations later
+  }
+  cp_async_wait<0>();
+  if (!A.final_pass) return;
+  const unsigned nblk = gridDim.x;
+  if (A.norm) {
+    double sblk = block_sum(acc, red);
+    if (threadIdx.x == 0) A.partial[blockIdx.x] = sblk;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned ticket = atomicAdd(A.counter, 1u);
+    am_last = (ticket == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (A.norm) {
+    double sum = 0.0;
+    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) sum += __ldcg(A.partial + i);
+    sum = block_sum(sum, red);
+    if (threadIdx.x == 0) {
+      const double norm = A.prm[PRM_CELL] * sum;
+      if (norm > 0.0 && isfinite(norm)) A.prm[PRM_SC] = 1.0 / sqrt(norm);
+      else A.prm[PRM_NONFINITE] = 1.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    *A.step += 1;
+    *A.counter = 0u;
+  }
 }
 
 // ------------------------------------------------------------ observables
