@@ -68,6 +68,12 @@ extern "C" {
 /* dgpe_params.flags */
 #define DGPE_FLAG_NO_GRAPH 1u   /* launch the passes directly instead of
                                    replaying a captured CUDA graph */
+#define DGPE_FLAG_CN_SERIAL 2u  /* FP64 form: solve every CN line serially,
+                                   one thread per line (the default once the
+                                   grid has >= 8192 lines per axis); the FP32
+                                   form returns DGPE_EUNSUPPORTED */
+#define DGPE_FLAG_CN_CHUNKED 4u /* FP64 form: always use the chunk-parallel
+                                   CN solve (exclusive with CN_SERIAL) */
 
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */

@@ -28,7 +28,7 @@ struct Cls {
   SArgs<float> *dS = nullptr;
   CArgs<float> *dC = nullptr;
   int LP = 0, xT = 0, xgrid = 0, sW = 0, sT = 0, cW = 0, cT = 0;
-  size_t xs = 0, ss = 0, cs = 0;
+  size_t xs = 0, x4s = 0, ss = 0, cs = 0;
   dim3 sgrid, cgrid;
   cudaStream_t st = nullptr;
 };
@@ -93,6 +93,7 @@ int configure(dgpe_batch *b, Cls &c, int LP, int sW, int cW) {
   c.xT = 2 * LP * TPL;
   c.xgrid = ((e0->nrows + 1) / 2 + LP - 1) / LP;
   c.xs = sizeof(Cx) * (size_t)(LP * e0->x_pitchz + 2 * LP * e0->x_pitch);
+  c.x4s = sizeof(Cx) * (size_t)(LP * e0->x_pitchz);
   const int es = variant_ept_s(c.var, Eng::EPT_S);
   c.sW = sW;
   c.sT = sW * n / es;
@@ -133,7 +134,7 @@ int launch_class(dgpe_batch *b, Cls &c, cudaStream_t s) {
   int rc = with_xvar(c.var, [&](auto CLc, auto EXc, auto P2c) -> int {
     constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
     constexpr bool P2 = decltype(P2c)::value;
-    k_dens_r2c_x_batch<float, EX, P2><<<xg, c.xT, c.xs, s>>>(c.dX);
+    k_dens_r2c_x_batch<float, EX, P2><<<xg, c.xT, c.x4s, s>>>(c.dX);
     if (cudaPeekAtLastError() != cudaSuccess) return 1;
     with_svar<Eng::EPT_S>(c.var, [&](auto EPc, auto SP2c) -> int {
       constexpr int EP = decltype(EPc)::value;
@@ -170,7 +171,7 @@ int set_attrs(dgpe_batch *b, const Cls &c) {
     constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
     constexpr bool P2 = decltype(P2c)::value;
     const size_t xs = std::max<size_t>(c.xs, 1);
-    if (e == cudaSuccess) e = attr(k_dens_r2c_x_batch<float, EX, P2>, xs);
+    if (e == cudaSuccess) e = attr(k_dens_r2c_x_batch<float, EX, P2>, std::max<size_t>(c.x4s, 1));
     if (e == cudaSuccess) e = attr(k_c2r_x_exp_cnx_batch<float, float, EX, CL, P2>, xs);
     if (e == cudaSuccess) e = attr(k_c2r_x_exp_cnx_batch<float, Cx, EX, CL, P2>, xs);
     if (e == cudaSuccess) e = attr(k_cn_strided_batch<float, float, CL>, c.cs);

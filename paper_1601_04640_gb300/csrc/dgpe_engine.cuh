@@ -190,16 +190,21 @@ template <typename R> struct EngineT : Engine {
 
   // pass configurations
   int x_LP = 0, x_T = 0, x_TPL = 0, x_C = 0, x_pitchz = 0, x_pitch = 0, x_grid = 0;
-  size_t x_smem = 0;
+  size_t x_smem = 0, x4_smem = 0;  // the C2R/exp/CN pass; the density pass (Z tile only)
   struct CnCfg {
     int n, ncols, W, TPL, C, pitch, T;
     long long es, os;
     dim3 grid;
-    size_t smem;
+    size_t smem;   // one tile
     int pgrid[2];  // persistent grid of the double-buffered kernel (real, complex coefficients)
   };
   int nsm = 1;
   CnCfg cn[3];   // index = axis (0 unused: x is fused into P1)
+  // line-serial CN (one thread per line, k_cn_lines), used by the FP64 form on
+  // grids with enough lines to fill the GPU; x is then a pass of its own
+  struct LnCfg { int n, ncols, T; long long es, cs, os; dim3 grid; };
+  LnCfg ln[3];
+  bool cn_serial = false;
   struct FtCfg { int n, T, W; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
   FtCfg fy{}, fz{};
   int obs_rows = 1, obs_blocks = 0, ndip = 0;
@@ -226,7 +231,7 @@ template <typename R> struct EngineT : Engine {
   size_t sites() const override { return nsites; }
 
   int launches_per_step() const override {
-    int k = 1 + (dim == 3 ? 2 : 1);  // P1, CN passes
+    int k = 1 + (dim == 3 ? 2 : 1) + (cn_serial ? 1 : 0);  // P1, CN passes
     if (has_dip) k += (dim == 3 ? 4 : 2);
     return k;
   }
@@ -322,12 +327,14 @@ template <typename R> struct EngineT : Engine {
     x_pitchz = nx + nx / PW + 1;
     x_pitch = nx + nx / x_C + 1;
     x_smem = sizeof(Cx) * (size_t)(x_LP * x_pitchz + 2 * x_LP * x_pitch);
+    x4_smem = sizeof(Cx) * (size_t)(x_LP * x_pitchz);
     {
       const int npairs = (nrows + 1) / 2;
       x_grid = (npairs + x_LP - 1) / x_LP;
     }
     if ((rc = make_cn_cfg(1))) return rc;
     if (dim == 3 && (rc = make_cn_cfg(2))) return rc;
+    if ((rc = choose_cn_form())) return rc;
     if ((rc = build_cn_tables())) return rc;
     fy.axis = 1;
     fz.axis = 2;
@@ -355,9 +362,11 @@ template <typename R> struct EngineT : Engine {
     const FtCfg &last = (dim == 3) ? fz : fy;
     ndip = has_dip ? (int)(last.grid.x * last.grid.y) : 0;
     const CnCfg &fin = cn[dim == 3 ? 2 : 1];
+    const LnCfg &lfin = ln[dim == 3 ? 2 : 1];
     // norm partials of the final pass (twice its default grid: a batch may run
     // the pass with half-width tiles)
-    if ((rc = dalloc(&partial, 2 * (size_t)fin.grid.x * fin.grid.y))) return rc;
+    if ((rc = dalloc(&partial, std::max(2 * (size_t)fin.grid.x * fin.grid.y,
+                                        cn_serial ? (size_t)lfin.grid.x * lfin.grid.y : (size_t)0)))) return rc;
     if ((rc = dalloc(&obs_part, (size_t)obs_blocks * OBS_COUNT))) return rc;
     if ((rc = dalloc(&dip_part, (size_t)std::max(ndip, 1)))) return rc;
     if ((rc = dalloc(&obs_out, OBS_COUNT + 1))) return rc;
@@ -369,6 +378,34 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
 
+  // The FP64 form solves each line serially once there are enough lines for
+  // one warp per SM sub-partition at least (it is FP64-pipe-bound, and the
+  // serial solve does half the arithmetic); flags force either form.
+  int choose_cn_form() {
+    const size_t lines_min = nsites / (size_t)std::max(nx, std::max(ny, nz));
+    if ((p.flags & DGPE_FLAG_CN_SERIAL) && (p.flags & DGPE_FLAG_CN_CHUNKED)) {
+      err = "DGPE_FLAG_CN_SERIAL and DGPE_FLAG_CN_CHUNKED are exclusive";
+      return DGPE_EINVAL;
+    }
+    if (sizeof(R) == 4) {
+      if (p.flags & DGPE_FLAG_CN_SERIAL) { err = "the line-serial CN solve is an FP64-form option"; return DGPE_EUNSUPPORTED; }
+      cn_serial = false;
+    } else if (p.flags & DGPE_FLAG_CN_SERIAL) cn_serial = true;
+    else if (p.flags & DGPE_FLAG_CN_CHUNKED) cn_serial = false;
+    else cn_serial = lines_min >= 8192;
+    const int ns[3] = {nx, ny, nz};
+    for (int a = 0; a < dim; ++a) {
+      LnCfg &L = ln[a];
+      L.n = ns[a];
+      if (a == 0) { L.ncols = (int)nrows; L.es = 1; L.cs = nx; L.os = 0; }
+      else if (a == 1) { L.ncols = nx; L.es = nx; L.cs = 1; L.os = (long long)nx * ny; }
+      else { L.ncols = nx; L.es = (long long)nx * ny; L.cs = 1; L.os = nx; }
+      L.T = std::min(128, (L.ncols + 31) / 32 * 32);
+      const unsigned outer = (a == 0) ? 1u : (a == 1 ? (unsigned)nz : (unsigned)ny);
+      L.grid = dim3((unsigned)((L.ncols + L.T - 1) / L.T), outer);
+    }
+    return DGPE_OK;
+  }
   int make_cn_cfg(int axis) {
     CnCfg &c = cn[axis];
     const int n = (axis == 1) ? ny : nz;
@@ -495,12 +532,13 @@ template <typename R> struct EngineT : Engine {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
       int r;
-      if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2>, x_smem))) return r;
-      if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2>, x4_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2>, x4_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2>, x_smem))) return r;
       return DGPE_OK;
     });
     if (rc) return rc;
@@ -520,16 +558,18 @@ template <typename R> struct EngineT : Engine {
       rc = with_cl(var[a], [&](auto CLc) -> int {
         constexpr int CL = decltype(CLc)::value;
         int r;
-        if ((r = smem_attr(k_cn_strided<R, R, CL>, cn[a].smem))) return r;
-        if ((r = smem_attr(k_cn_strided<R, Cx, CL>, cn[a].smem))) return r;
-        if ((r = smem_attr(k_cn_strided_pipe<R, R, CL>, 2 * cn[a].smem))) return r;
-        if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL>, 2 * cn[a].smem))) return r;
-        // persistent grid: as many CTAs as fit on the device, at most one per tile
+        const size_t one = cn[a].smem, two = 2 * cn[a].smem;
+        if ((r = smem_attr(k_cn_strided<R, R, CL>, one))) return r;
+        if ((r = smem_attr(k_cn_strided<R, Cx, CL>, one))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, R, CL>, two))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL>, two))) return r;
+        // persistent grid: as many CTAs as fit on the device, at most one per
+        // tile, each double-buffered (the next tile is prefetched)
         const int ntiles = (int)(cn[a].grid.x * cn[a].grid.y);
         int occ = 0;
-        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, R, CL>, cn[a].T, 2 * cn[a].smem));
+        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, R, CL>, cn[a].T, two));
         cn[a].pgrid[0] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
-        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, Cx, CL>, cn[a].T, 2 * cn[a].smem));
+        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, Cx, CL>, cn[a].T, two));
         cn[a].pgrid[1] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
         return DGPE_OK;
       });
@@ -571,6 +611,7 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
   int launch_cn(int axis, bool final_pass, cudaStream_t s, Cx *buf = nullptr, bool adjoint = false) {
+    if (cn_serial) return launch_lines(axis, final_pass, s, buf, adjoint);
     const CnCfg &c = cn[axis];
     CArgs<R> A{};
     A.psi = buf ? buf : psi; A.cntab = adjoint ? cntab_adj[axis] : cntab[axis];
@@ -588,6 +629,19 @@ template <typename R> struct EngineT : Engine {
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
+  int launch_lines(int axis, bool final_pass, cudaStream_t s, Cx *buf, bool adjoint) {
+    const LnCfg &L = ln[axis];
+    LArgs A{};
+    A.psi = buf ? buf : psi; A.tab = adjoint ? cntab_adj[axis] : cntab[axis];
+    A.prm = prm; A.partial = partial; A.counter = counter; A.step = dstep;
+    A.es = L.es; A.cs = L.cs; A.os = L.os; A.n = L.n; A.ncols = L.ncols;
+    A.final_pass = final_pass ? 1 : 0; A.norm = (final_pass && imag) ? 1 : 0;
+    A.tau = adjoint ? -tau[axis] : tau[axis];
+    if (imag) k_cn_lines<R, R><<<L.grid, L.T, 0, s>>>(A);
+    else k_cn_lines<R, Cx><<<L.grid, L.T, 0, s>>>(A);
+    DGPE_LCK(__func__);
+    return DGPE_OK;
+  }
   // density (of `src`, or the real field `dens_in`) -> half spectrum along x
   int launch_forward_spectrum(cudaStream_t s, const Cx *src = nullptr, const R *dens_in = nullptr) {
     XArgs<R> A = xargs();
@@ -596,15 +650,17 @@ template <typename R> struct EngineT : Engine {
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      if (dens_in) k_dens_r2c_x<R, EX, 1, P2><<<x_grid, x_T, x_smem, s>>>(A);
-      else k_dens_r2c_x<R, EX, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      if (dens_in) k_dens_r2c_x<R, EX, 1, P2><<<x_grid, x_T, x4_smem, s>>>(A);
+      else k_dens_r2c_x<R, EX, 0, P2><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
-  // mode 0: step pass on psi; 1: Phi_d into phi_out; 2: CN_x (conjugated) on buf
+  // mode 0: step pass on psi; 1: Phi_d into phi_out; 2: CN_x (conjugated) on
+  // buf; 3: step pass without CN_x (the line-serial CN_x pass follows)
   int launch_p1(int mode, cudaStream_t s, Cx *buf = nullptr, R *phi_out = nullptr) {
+    if (mode == 2 && cn_serial) return launch_lines(0, false, s, buf, true);
     XArgs<R> A = xargs();
     if (buf) A.psi = buf;
     if (phi_out) A.phi_out = phi_out;
@@ -618,6 +674,8 @@ template <typename R> struct EngineT : Engine {
       if (mode == 0) {
         if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
         else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+      } else if (mode == 3) {
+        k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 1) {
         k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2><<<x_grid, x_T, x_smem, s>>>(A);
       } else {
@@ -642,7 +700,7 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
   // The passes of one step, in order (id, name, algorithmic HBM bytes).
-  enum { PS_DENS_R2C, PS_FFT_Y, PS_FFT_Z_U, PS_IFFT_Y, PS_FFT_Y_U, PS_P1, PS_CN_Y, PS_CN_Z };
+  enum { PS_DENS_R2C, PS_FFT_Y, PS_FFT_Z_U, PS_IFFT_Y, PS_FFT_Y_U, PS_P1, PS_CN_Y, PS_CN_Z, PS_P1_NOCN, PS_CN_X };
   std::vector<int> pass_ids() const {
     std::vector<int> v;
     if (has_dip) {
@@ -650,7 +708,8 @@ template <typename R> struct EngineT : Engine {
       if (dim == 3) { v.push_back(PS_FFT_Y); v.push_back(PS_FFT_Z_U); v.push_back(PS_IFFT_Y); }
       else v.push_back(PS_FFT_Y_U);
     }
-    v.push_back(PS_P1);
+    if (cn_serial) { v.push_back(PS_P1_NOCN); v.push_back(PS_CN_X); }
+    else v.push_back(PS_P1);
     v.push_back(PS_CN_Y);
     if (dim == 3) v.push_back(PS_CN_Z);
     return v;
@@ -663,6 +722,8 @@ template <typename R> struct EngineT : Engine {
       case PS_IFFT_Y: return launch_fft(fy, 1, s);
       case PS_FFT_Y_U: return launch_fft(fy, 2, s);
       case PS_P1: return launch_p1(0, s);
+      case PS_P1_NOCN: return launch_p1(3, s);
+      case PS_CN_X: return launch_cn(0, false, s);
       case PS_CN_Y: return launch_cn(1, dim == 2, s);
       default: return launch_cn(2, true, s);
     }
@@ -676,7 +737,7 @@ template <typename R> struct EngineT : Engine {
   }
   const char *pass_name(int i) const override {
     static const char *names[] = {"dens_r2c_x", "fft_y", "fft_z_u_ifft_z", "ifft_y",
-                                  "fft_y_u_ifft_y", "c2r_x_exp_cn_x", "cn_y", "cn_z"};
+                                  "fft_y_u_ifft_y", "c2r_x_exp_cn_x", "cn_y", "cn_z", "c2r_x_exp", "cn_x"};
     std::vector<int> v = pass_ids();
     return (i >= 0 && i < (int)v.size()) ? names[v[i]] : "";
   }
@@ -689,7 +750,7 @@ template <typename R> struct EngineT : Engine {
       case PS_DENS_R2C: return N * S + sp * S;
       case PS_FFT_Y: case PS_IFFT_Y: return 2.0 * sp * S;
       case PS_FFT_Z_U: case PS_FFT_Y_U: return 2.0 * sp * S + ub;
-      case PS_P1: return (has_dip ? sp * S : 0.0) + 2.0 * N * S;
+      case PS_P1: case PS_P1_NOCN: return (has_dip ? sp * S : 0.0) + 2.0 * N * S;
       default: return 2.0 * N * S;
     }
   }

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_dens_r2c_x_batch(co
 // ------------------------------------------------------------------ P1
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
 // MODE 2: CN_x alone (the reverse step applies it to the adjoint field).
+// MODE 3: C2R_x and the exponential, no CN (a separate CN_x pass follows).
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2>
 __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -215,7 +216,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   constexpr bool TAB = (sizeof(R) == 8);
   // FP32: shared copy of the m table (the CN solve forms the rest in registers)
   __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
-  if (!TAB && MODE != 1) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), A.nx);
+  if (!TAB && MODE != 1 && MODE != 3) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), A.nx);
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
   const int ln = POW2 ? ilog2(n) : 0;
   const int p0 = blockIdx.x * A.LP;
@@ -289,6 +290,15 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     __syncthreads();
   }
   if (MODE == 1) return;
+  if (MODE == 3) {
+    __syncthreads();
+    for (int idx = t; idx < 2 * A.LP * n; idx += T) {
+      const int L = row_of(idx), a = col_of(idx);
+      const int row = 2 * p0 + L;
+      if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
+    }
+    return;
+  }
   // Crank-Nicolson along x: TPL lanes per line
   const int l = t / A.TPL, q = t - l * A.TPL;
   const bool active = (2 * p0 + l) < nrows;
@@ -543,6 +553,150 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_pipe(CAr
     }
   }
   if (threadIdx.x == 0) {
+    *A.step += 1;
+    *A.counter = 0u;
+  }
+}
+
+// ------------------------------------------ line-serial Crank-Nicolson
+// One thread per grid line, streaming the line through registers: the Thomas
+// algorithm in its textbook form (Sec. 2, the tridiagonal solve of each CN
+// half-step), with the right-hand side B psi formed on the fly,
+//   d_a  = psi_a + kt (psi_{a-1} - 2 psi_a + psi_{a+1}),
+//   d'_a = m_a (d_a + kt d'_{a-1}),        m_a = 1 / (1 + 2 kt - kt^2 m_{a-1}),
+//   x_a  = d'_a + (kt m_a) x_{a+1},
+// d' written over psi in place and read back by the same thread.  It executes
+// about half the arithmetic of the chunk-parallel solve (no scan, no
+// correction sweeps), which is what bounds the FP64 form: that form is limited
+// by the FP64 pipe, not by memory.  Neighbouring threads own neighbouring
+// lines, so a y or z sweep reads and writes one coalesced segment per warp and
+// step; an x sweep walks rows (every access of a warp hits 32 rows, each row's
+// 128-byte line staying in L1 for the next steps).  Loads run LS_K sites
+// ahead of the stores, from registers.  tab holds m (n values) then kt m (n).
+struct LArgs {
+  void *psi;
+  const void *tab;
+  double *prm;
+  double *partial;
+  unsigned *counter;
+  long long *step;
+  long long es;  // element stride along a line
+  long long cs;  // stride between neighbouring lines
+  long long os;  // stride of the outer index (blockIdx.y)
+  int n, ncols, final_pass, norm;
+  double tau;
+};
+#define DGPE_LS_K 8
+
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+// kt v (+ w) for kt = tau (imaginary time, real Coef) or kt = i tau (real time)
+template <typename R, typename Coef> struct KtMul;
+template <typename R> struct KtMul<R, R> {
+  static __device__ __forceinline__ cx<R> mul(R tau, cx<R> v) { return mk<R>(tau * v.x, tau * v.y); }
+  static __device__ __forceinline__ cx<R> fma(R tau, cx<R> v, cx<R> w) {
+    return mk<R>(fma_r(tau, v.x, w.x), fma_r(tau, v.y, w.y));
+  }
+};
+template <typename R> struct KtMul<R, cx<R>> {
+  static __device__ __forceinline__ cx<R> mul(R tau, cx<R> v) { return mk<R>(-tau * v.y, tau * v.x); }
+  static __device__ __forceinline__ cx<R> fma(R tau, cx<R> v, cx<R> w) {
+    return mk<R>(fma_r(-tau, v.y, w.x), fma_r(tau, v.x, w.y));
+  }
+};
+
+template <typename R, typename Coef>
+__global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
+  __shared__ double red[32];
+  __shared__ int am_last;
+  typedef cx<R> Cx;
+  typedef KtMul<R, Coef> KT;
+  constexpr int K = DGPE_LS_K;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = A.n;
+  const long long es = A.es;
+  const R tau = (R)A.tau;
+  const Coef *tm = reinterpret_cast<const Coef *>(A.tab), *ta = tm + n;
+  double acc = 0.0;
+  if (c < A.ncols) {
+    Cx *p = reinterpret_cast<Cx *>(A.psi) + (size_t)blockIdx.y * A.os + (size_t)c * A.cs;
+    // forward elimination; buf[i] holds psi_{a0 + 1 + i}
+    Cx buf[K], nb[K];
+    Cx prev = czero<Cx>(), cur = p[0], dp = czero<Cx>();
+#pragma unroll
+    for (int i = 0; i < K; ++i) buf[i] = (1 + i < n) ? p[(size_t)(1 + i) * es] : czero<Cx>();
+    for (int a0 = 0; a0 < n; a0 += K) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = a0 + K + 1 + i;
+        nb[i] = (j < n) ? p[(size_t)j * es] : czero<Cx>();
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int a = a0 + i;
+        if (a < n) {
+          const Cx nxt = buf[i];
+          const Cx lap = (prev + nxt) - cur - cur;
+          const Cx d = KT::fma(tau, lap, cur);
+          dp = coef_mul(__ldg(tm + a), KT::fma(tau, dp, d));
+          p[(size_t)a * es] = dp;
+          prev = cur;
+          cur = nxt;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) buf[i] = nb[i];
+    }
+    // back substitution; buf[i] holds d'_{a0 - i}
+    Cx x = czero<Cx>();
+#pragma unroll
+    for (int i = 0; i < K; ++i) buf[i] = (n - 1 - i >= 0) ? p[(size_t)(n - 1 - i) * es] : czero<Cx>();
+    for (int a0 = n - 1; a0 >= 0; a0 -= K) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = a0 - K - i;
+        nb[i] = (j >= 0) ? p[(size_t)j * es] : czero<Cx>();
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int a = a0 - i;
+        if (a >= 0) {
+          x = buf[i] + coef_mul(__ldg(ta + a), x);
+          p[(size_t)a * es] = x;
+          if (A.norm) acc += (double)x.x * x.x + (double)x.y * x.y;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) buf[i] = nb[i];
+    }
+  }
+  if (!A.final_pass) return;
+  const int t = threadIdx.x, T = blockDim.x;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (A.norm) {
+    const double sblk = block_sum(acc, red);
+    if (t == 0) A.partial[bid] = sblk;
+  }
+  if (t == 0) {
+    __threadfence();
+    const unsigned ticket = atomicAdd(A.counter, 1u);
+    am_last = (ticket == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (A.norm) {
+    double sum = 0.0;
+    for (unsigned i = t; i < nblk; i += T) sum += __ldcg(A.partial + i);
+    sum = block_sum(sum, red);
+    if (t == 0) {
+      const double norm = A.prm[PRM_CELL] * sum;
+      if (norm > 0.0 && isfinite(norm)) A.prm[PRM_SC] = 1.0 / sqrt(norm);
+      else A.prm[PRM_NONFINITE] = 1.0;
+    }
+  }
+  if (t == 0) {
     *A.step += 1;
     *A.counter = 0u;
   }

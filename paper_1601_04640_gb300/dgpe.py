@@ -33,6 +33,8 @@ DGPE_KERNEL_QUASI2D_XY = 2
 DGPE_PLANE_XY = 0
 DGPE_PLANE_XZ = 1
 DGPE_FLAG_NO_GRAPH = 1
+DGPE_FLAG_CN_SERIAL = 2
+DGPE_FLAG_CN_CHUNKED = 4
 
 EXPORTS = [
     "dgpe_create", "dgpe_destroy", "dgpe_set_psi", "dgpe_get_psi", "dgpe_set_psi_device",
@@ -124,7 +126,8 @@ def _check(rc, h=None):
 
 
 def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                kernel=None, qd=0.5, graph=True):
+                kernel=None, qd=0.5, graph=True, cn=None):
+    """cn: None (automatic), "serial" or "chunked" (FP64 Crank-Nicolson form)."""
     p = dgpe_params()
     p.dim = dim
     p.plane = DGPE_PLANE_XY
@@ -141,6 +144,12 @@ def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
     p.kernel = kernel
     p.qd = float(qd)
     p.flags = 0 if graph else DGPE_FLAG_NO_GRAPH
+    if cn == "serial":
+        p.flags |= DGPE_FLAG_CN_SERIAL
+    elif cn == "chunked":
+        p.flags |= DGPE_FLAG_CN_CHUNKED
+    elif cn is not None:
+        raise ValueError("cn must be None, 'serial' or 'chunked'")
     return p
 
 
@@ -254,11 +263,11 @@ class Solver:
     """One condensate on the GPU: create, set/get psi, step, observe."""
 
     def __init__(self, dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                 kernel=None, qd=0.5, graph=True, stream: int = 0):
+                 kernel=None, qd=0.5, graph=True, stream: int = 0, cn=None):
         self.dim = dim
         self.n = tuple(n)
         self.shape = (n[2], n[1], n[0]) if dim == 3 else (n[1], n[0])
-        self.params = make_params(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel, qd, graph)
+        self.params = make_params(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel, qd, graph, cn)
         self.h = dgpe_create(self.params, stream)
 
     def close(self):

@@ -22,7 +22,8 @@ def _states():
     return cm, psi0, target
 
 
-def test_step_adjoint_matches_oracle():
+@pytest.mark.parametrize("cn", [None, "serial"])
+def test_step_adjoint_matches_oracle(cn):
     torch = pytest.importorskip("torch")
     gbuild.build()
     cm, psi0, target = _states()
@@ -31,7 +32,7 @@ def test_step_adjoint_matches_oracle():
     Gp = rng.standard_normal(psi0.shape) + 1j * rng.standard_normal(psi0.shape)
     step = 7
     ref_G, ref_dg, ref_dc = oracle.step_adjoint(op, psi0, Gp, step)
-    with dgpe.Solver(3, N, H, NU, G0, GDD, DT, False, True) as s:
+    with dgpe.Solver(3, N, H, NU, G0, GDD, DT, False, True, cn=cn) as s:
         s.set_trap_modulation(cm)
         pin = torch.from_numpy(psi0).cuda()
         G = torch.from_numpy(Gp).cuda()

@@ -38,8 +38,8 @@ def make_case(dim, n, h, nu, g, gdd, dt, imag, kernel=None, seed=1601, noise=0.0
     return op, kc, psi0
 
 
-def gpu_run(dim, n, h, nu, g, gdd, dt, imag, fp64, kc, psi0, steps, graph=True):
-    with dgpe.Solver(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel=kc, graph=graph) as s:
+def gpu_run(dim, n, h, nu, g, gdd, dt, imag, fp64, kc, psi0, steps, graph=True, cn=None):
+    with dgpe.Solver(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel=kc, graph=graph, cn=cn) as s:
         s.set_psi(psi0)
         s.step(steps)
         return s.get_psi(), s.observables()
@@ -93,6 +93,49 @@ def test_step_parity_3d(fp64, imag, case):
         assert e < TOL_PSI[fp64]
 
 
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("case", range(len(CASES_3D)))
+def test_step_parity_3d_line_serial_cn(imag, case):
+    """FP64 form with the one-thread-per-line Thomas solve forced on small
+    grids (it is the default from 8192 lines per axis)."""
+    n, h, nu = CASES_3D[case]
+    op, kc, psi0 = make_case(3, n, h, nu, 50.0, 15.0, 2e-3, imag)
+    for steps in (1, 10):
+        psi, obs = gpu_run(3, n, h, nu, 50.0, 15.0, 2e-3, imag, True, kc, psi0, steps, cn="serial")
+        ref = oracle.step(op, psi0, 0, steps)
+        e = rel_l2(psi, ref)
+        print("steps", steps, "rel L2", e)
+        assert e < TOL_PSI[True]
+
+
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("n", [(64, 32), (96, 160)])
+def test_step_parity_2d_line_serial_cn(imag, n):
+    h, nu = (0.2, 0.3), (1.0, 1.5)
+    op, kc, psi0 = make_case(2, n, h, nu, 80.0, 40.0, 1e-3, imag)
+    psi, obs = gpu_run(2, n, h, nu, 80.0, 40.0, 1e-3, imag, True, kc, psi0, 10, cn="serial")
+    ref = oracle.step(op, psi0, 0, 10)
+    e = rel_l2(psi, ref)
+    print("rel L2", e)
+    assert e < TOL_PSI[True]
+
+
+def test_cn_form_flags_checked():
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    with pytest.raises(dgpe.DgpeError):
+        dgpe.Solver(3, n, h, nu, 1, 1, 1e-3, True, False, cn="serial")  # FP32 form
+    p = dgpe.make_params(3, n, h, nu, fp64=True)
+    p.flags |= dgpe.DGPE_FLAG_CN_SERIAL | dgpe.DGPE_FLAG_CN_CHUNKED
+    with pytest.raises(dgpe.DgpeError):
+        dgpe.dgpe_create(p)
+    # the line-serial form adds the CN_x pass
+    with dgpe.Solver(3, n, h, nu, 1, 1, 1e-3, True, True, cn="serial") as a, \
+            dgpe.Solver(3, n, h, nu, 1, 1, 1e-3, True, True, cn="chunked") as b:
+        la = dgpe.load().dgpe_launches_per_step(a.h)
+        lb = dgpe.load().dgpe_launches_per_step(b.h)
+        assert la == lb + 1
+
+
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("n", [(64, 32), (96, 160), (384, 80), (512, 64)])
@@ -106,15 +149,17 @@ def test_step_parity_2d(fp64, imag, n):
     assert e < TOL_PSI[fp64]
 
 
-@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "fp64_serial"])
 @pytest.mark.parametrize("imag", [True, False])
-def test_cn_only(fp64, imag):
+def test_cn_only(form, imag):
     """g = g_dd = 0, no trap: the exponential is the identity and the step is
     the three CN substeps alone (large dt so the solves are far from I)."""
+    fp64 = form != "fp32"
     n, h = (32, 64, 32), (0.2, 0.15, 0.3)
     op, kc, psi0 = make_case(3, n, h, (0, 0, 0), 0, 0, 0.05, imag, kernel="none", noise=0.3,
                              widths=(1.0, 1.0, 1.0))
-    psi, _ = gpu_run(3, n, h, (0, 0, 0), 0, 0, 0.05, imag, fp64, kc, psi0, 3)
+    psi, _ = gpu_run(3, n, h, (0, 0, 0), 0, 0, 0.05, imag, fp64, kc, psi0, 3,
+                     cn="serial" if form == "fp64_serial" else None)
     ref = oracle.step(op, psi0, 0, 3)
     e = rel_l2(psi, ref)
     print("rel L2", e)
@@ -166,10 +211,10 @@ def test_real3d_256_short_parity():
     op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=150, gdd=60, dt=5e-4, imag=False, kernel="dipolar3d")
     psi0 = synth.gaussian_state(n, h, (0.6, 0.6, 0.3), 0.01, 2000)
     ref = oracle.step(op, psi0, 0, 3)
-    for fp64 in (True, False):
-        psi, o = gpu_run(3, n, h, nu, 150, 60, 5e-4, False, fp64, None, psi0, 3)
+    for fp64, cn in ((True, None), (True, "chunked"), (False, None)):
+        psi, o = gpu_run(3, n, h, nu, 150, 60, 5e-4, False, fp64, None, psi0, 3, cn=cn)
         e = rel_l2(psi, ref)
-        print("fp64" if fp64 else "fp32", "rel L2", e)
+        print("fp64" if fp64 else "fp32", cn, "rel L2", e)
         assert e < TOL_PSI[fp64]
 
 
