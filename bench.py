@@ -60,6 +60,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def fp64_peak():
+    """FP64 arithmetic peak from unit counts and clocks: 152 SMs x 2 FP64
+    FMA per SM per clock (ncu's sm__sass_thread_inst_executed_op_dfma_pred_on
+    peak_sustained = 304 per clock for the GPU) x 2 flop x the maximum SM
+    clock (MEASURED_PEAKS.json sm_max_mhz, else the nominal 2070 MHz)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
 def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1601_04640_gb300", "csrc")
@@ -269,12 +283,28 @@ def main():
                 "traffic": ncu_traffic(top[0], name, args.workload),
                 "algorithmic_bytes_per_launch": top[2], "ms_per_launch": top[1]}
         step_bytes = sum(p[2] for p in passes)
+        step_flops = sum(p[3] for p in passes)
+        roof_alu = None
+        if fp64:
+            # the FP64 form is limited by the FP64 pipe: its roofline is the
+            # FP64 arithmetic peak (unit counts x clock)
+            pk = fp64_peak()
+            ach = top[3] / (top[1] * 1e-3) / 1e12
+            roof_alu = {"bound": "alu", "kernel": top[0], "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                        "frac": ach / pk, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                        "traffic": roof["traffic"], "algorithmic_flops_per_launch": top[3],
+                        "ms_per_launch": top[1]}
         f = {"value": world * sites * args.steps / (ms_max * 1e-3), "ms_per_step": ms_max / args.steps,
-             "dtype": "f64" if fp64 else "f32 (FP64 reductions/tables)", "roofline": roof,
+             "dtype": "f64" if fp64 else "f32 (FP64 reductions/tables)",
+             "roofline": roof_alu if roof_alu else roof,
+             "roofline_hbm": roof,
              "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
                           "achieved_GBps": step_bytes / (ms_max / args.steps * 1e-3) / 1e9,
                           "frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / hbm_peak},
-             "passes": [{"kernel": p[0], "ms": p[1], "share": p[1] / tot, "GBps": p[2] / (p[1] * 1e-3) / 1e9}
+             "step_flops": {"flops_per_step": step_flops,
+                            "achieved_TFLOPs": step_flops / (ms_max / args.steps * 1e-3) / 1e12},
+             "passes": [{"kernel": p[0], "ms": p[1], "share": p[1] / tot, "GBps": p[2] / (p[1] * 1e-3) / 1e9,
+                         "TFLOPs": p[3] / (p[1] * 1e-3) / 1e12}
                         for p in passes],
              "gpu_launches": launches, "clocks": clocks,
              "observables_after": {"norm": obs["norm"], "mu": obs["mu"], "energy": obs["energy"]}}
@@ -357,9 +387,10 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
                                                       "mu": prep["mu"]}},
-        "roofline": a["roofline"], "step_hbm": a["step_hbm"], "passes": a["passes"],
+        "roofline": a["roofline"], "roofline_hbm": a["roofline_hbm"], "step_hbm": a["step_hbm"],
+        "step_flops": a["step_flops"], "passes": a["passes"],
         "cpu_baseline": cpu, "e2e": a.get("e2e"),
-        "gpu_launches": a["gpu_launches"] + (b["gpu_launches"] if b else 0),
+        "gpu_launches": a["gpu_launches"],
         "clocks": a["clocks"], "observables_after": a["observables_after"],
         "fp32_bulk": b,
         "cufft_plain_step": plain,

@@ -168,6 +168,13 @@ int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap);
 const char *dgpe_pass_name(dgpe_t h, int i);
 double dgpe_pass_bytes(dgpe_t h, int i);
 
+/* Floating-point operations of pass i per launch, an FMA counting 2: the
+ * operation count of the pass's algorithm (FFT codelets and twiddles, pair
+ * packing of the real transforms, the exponential substep with sin and
+ * cos - 1 by Taylor series (expm1 counted as one operation), the Thomas
+ * recurrences).  0 for an index out of range or a NULL handle. */
+double dgpe_pass_flops(dgpe_t h, int i);
+
 /* Reverse mode of one real-time step (the adjoint form: Wirtinger
  * convention G = 2 dL/dpsi*).  psi_in: device state at the start of step
  * `step` (complex128 for DGPE_FP64, complex64 for DGPE_FP32_BULK); G: device

@@ -187,6 +187,7 @@ extern "C" int dgpe_profile_steps(dgpe_t h, int n, double *pass_ms, int cap) {
 extern "C" const char *dgpe_pass_name(dgpe_t h, int i) { return h ? h->eng->pass_name(i) : ""; }
 
 extern "C" double dgpe_pass_bytes(dgpe_t h, int i) { return h ? h->eng->pass_bytes(i) : 0.0; }
+extern "C" double dgpe_pass_flops(dgpe_t h, int i) { return h ? h->eng->pass_flops(i) : 0.0; }
 
 extern "C" int dgpe_step_adjoint(dgpe_t h, const void *psi_in, void *G, long long step, double *dL_dg,
                                  double *dL_dc) {

@@ -43,6 +43,7 @@ struct Engine {
                                 double *F, double *dFdg, double *dFdc, cudaStream_t s) = 0;
   virtual const char *pass_name(int i) const = 0;
   virtual double pass_bytes(int i) const = 0;
+  virtual double pass_flops(int i) const = 0;
   virtual size_t sites() const = 0;
   std::string err;
 };
@@ -452,7 +453,8 @@ template <typename R> struct EngineT : Engine {
     return upload(U, hu);
   }
 
-  // Crank-Nicolson LU and chunk-scan tables for axis a: m, alpha, P, Q.
+  // Crank-Nicolson LU and chunk-scan tables for axis a: m, alpha, P, Q (n
+  // each), then the middle-row pivot mu of the two-ended elimination.
   int build_cn_tables() {
     const int ns[3] = {nx, ny, nz};
     const int Cs[3] = {x_C, cn[1].C, dim == 3 ? cn[2].C : 1};
@@ -465,6 +467,12 @@ template <typename R> struct EngineT : Engine {
       m[0] = 1.0 / b;
       for (int i = 1; i < n; ++i) m[i] = 1.0 / (b - kt * kt * m[i - 1]);
       for (int i = 0; i < n; ++i) al[i] = kt * m[i];
+      // reciprocal pivot of the middle row k = n/2 when the line is
+      // eliminated from both ends at once (the matrix is persymmetric, so the
+      // bottom-up elimination has the same m and alpha, indexed from the end):
+      //   mu = 1 / (1 + 2kt - kt (alpha_{k-1} + alpha_{n-2-k}))
+      const int kmid = n / 2;
+      const zd mu = 1.0 / (b - kt * (al[kmid - 1] + al[n - 2 - kmid]));
       for (int c0 = 0; c0 < n; c0 += C) {
         zd pr = 1.0;
         for (int i = c0; i < c0 + C; ++i) { pr *= al[i]; P[i] = pr; }
@@ -472,35 +480,38 @@ template <typename R> struct EngineT : Engine {
         for (int i = c0 + C - 1; i >= c0; --i) { pr *= al[i]; Q[i] = pr; }
       }
       if (!cntab[a]) {
-        int rc = dalloc((Cx **)&cntab[a], 4 * (size_t)n);
+        int rc = dalloc((Cx **)&cntab[a], 4 * (size_t)n + 1);
         if (rc) return rc;
       }
       if (!imag) {
         // conjugated tables for the reverse step (C^dagger = B^dagger A^-dagger)
         if (!cntab_adj[a]) {
-          int rc = dalloc((Cx **)&cntab_adj[a], 4 * (size_t)n);
+          int rc = dalloc((Cx **)&cntab_adj[a], 4 * (size_t)n + 1);
           if (rc) return rc;
         }
-        std::vector<Cx> t(4 * (size_t)n);
+        std::vector<Cx> t(4 * (size_t)n + 1);
         auto put = [&](size_t i, zd v) { t[i].x = (R)v.real(); t[i].y = (R)(-v.imag()); };
         for (int i = 0; i < n; ++i) {
           put(i, m[i]); put(n + i, al[i]); put(2 * n + i, P[i]); put(3 * n + i, Q[i]);
         }
+        put(4 * (size_t)n, mu);
         DGPE_CK(cudaMemcpy(cntab_adj[a], t.data(), sizeof(Cx) * t.size(), cudaMemcpyHostToDevice));
       }
       if (imag) {
-        std::vector<R> t(4 * (size_t)n);
+        std::vector<R> t(4 * (size_t)n + 1);
         for (int i = 0; i < n; ++i) {
           t[i] = (R)m[i].real(); t[n + i] = (R)al[i].real();
           t[2 * n + i] = (R)P[i].real(); t[3 * n + i] = (R)Q[i].real();
         }
+        t[4 * (size_t)n] = (R)mu.real();
         DGPE_CK(cudaMemcpy(cntab[a], t.data(), sizeof(R) * t.size(), cudaMemcpyHostToDevice));
       } else {
-        std::vector<Cx> t(4 * (size_t)n);
+        std::vector<Cx> t(4 * (size_t)n + 1);
         auto put = [&](size_t i, zd v) { t[i].x = (R)v.real(); t[i].y = (R)v.imag(); };
         for (int i = 0; i < n; ++i) {
           put(i, m[i]); put(n + i, al[i]); put(2 * n + i, P[i]); put(3 * n + i, Q[i]);
         }
+        put(4 * (size_t)n, mu);
         DGPE_CK(cudaMemcpy(cntab[a], t.data(), sizeof(Cx) * t.size(), cudaMemcpyHostToDevice));
       }
     }
@@ -752,6 +763,71 @@ template <typename R> struct EngineT : Engine {
       case PS_FFT_Z_U: case PS_FFT_Y_U: return 2.0 * sp * S + ub;
       case PS_P1: case PS_P1_NOCN: return (has_dip ? sp * S : 0.0) + 2.0 * N * S;
       default: return 2.0 * N * S;
+    }
+  }
+  // Floating-point operations of pass i per launch (an FMA counts 2), from
+  // the arithmetic each algorithm specifies: Stockham FFT stages (codelet
+  // operation counts plus (r - 1) twiddle products per radix-r butterfly
+  // after the first stage), the pair packing/unpacking of the real
+  // transforms, the exponential substep, and the Thomas recurrences.
+  static double codelet_flops(int r) {
+    switch (r) {
+      case 2: return 4;     // one complex sum and difference
+      case 3: return 16;
+      case 4: return 16;    // 8 complex additions
+      case 5: return 48;
+      case 8: return 60;    // two radix-4 (32) + two w8 rotations (12) + 8 additions (16)
+      case 16: return 176;  // eight radix-4 (128) + eight inner twiddle rotations (48)
+      default: return 0;
+    }
+  }
+  static double fft_line_flops(const FftPlan &pl) {
+    double f = 0.0;
+    for (int s = 0; s < pl.ns; ++s) {
+      const double nb = (double)pl.n / pl.rad[s];
+      f += nb * codelet_flops(pl.rad[s]);
+      if (s > 0) f += nb * (pl.rad[s] - 1) * 6.0;
+    }
+    return f;
+  }
+  // exponential substep per site: scale (2), density (3), V (1), theta
+  // (5 with the dipolar term, else 3), the factor (real time: sin and
+  // cos - 1 by Taylor series, 19 in FP64 / 11 in FP32; imaginary time:
+  // expm1 counted as 1) and the increment update (8 real / 4 imaginary)
+  double exp_flops_per_site() const {
+    const double th = has_dip ? 5.0 : 3.0;
+    if (imag) return 2 + 3 + 1 + th + 1 + 4;
+    return 2 + 3 + 1 + th + (sizeof(R) == 8 ? 19.0 : 11.0) + 8;
+  }
+  // Thomas solve per site: line-serial (forward right-hand side, forward
+  // elimination, back substitution) or chunk-parallel (chunk passes, the two
+  // lane scans amortised over the chunk, fix-ups)
+  double cn_flops_per_site(int axis) const {
+    if (cn_serial) return imag ? 16.0 : 28.0;
+    const int cl = (axis == 0) ? x_C : cn[axis].C;
+    const int tpl = (axis == 0) ? x_TPL : cn[axis].TPL;
+    const double lg = std::log2((double)std::max(tpl, 1));
+    if (imag) return 28.0 + 2.0 * 5.0 * lg / cl;
+    return 52.0 + 2.0 * 14.0 * lg / cl;
+  }
+  double pass_flops(int i) const override {
+    std::vector<int> v = pass_ids();
+    if (i < 0 || i >= (int)v.size()) return 0.0;
+    const double N = (double)nsites, pairs = (double)((nrows + 1) / 2);
+    const double norm = (imag ? 4.0 : 0.0);  // FP64 |x|^2 accumulation of the final pass
+    switch (v[i]) {
+      case PS_DENS_R2C: return 4.0 * N + pairs * fft_line_flops(plx) + pairs * (nx / 2 + 1) * 8.0;
+      case PS_FFT_Y: case PS_IFFT_Y: return (double)ncol_spec * nz * fft_line_flops(ply);
+      case PS_FFT_Z_U: return (double)ncol_spec * ny * (2.0 * fft_line_flops(plz) + 2.0 * nz);
+      case PS_FFT_Y_U: return (double)ncol_spec * (2.0 * fft_line_flops(ply) + 2.0 * ny);
+      case PS_P1: case PS_P1_NOCN: {
+        double f = (has_dip ? pairs * fft_line_flops(plx) : 0.0) + N * exp_flops_per_site();
+        if (v[i] == PS_P1) f += N * cn_flops_per_site(0);
+        return f;
+      }
+      case PS_CN_X: return N * cn_flops_per_site(0);
+      case PS_CN_Y: return N * (cn_flops_per_site(1) + (dim == 2 ? norm : 0.0));
+      default: return N * (cn_flops_per_site(2) + norm);
     }
   }
   int profile_steps(int n, double *pass_ms, int cap, cudaStream_t s) override {

@@ -88,29 +88,44 @@ template <> __device__ __forceinline__ float make_kt<float>(double tau) { return
 template <> __device__ __forceinline__ double2 make_kt<double2>(double tau) { return make_double2(0.0, tau); }
 template <> __device__ __forceinline__ float2 make_kt<float2>(double tau) { return make_float2(0.0f, (float)tau); }
 
-// sin and cos of a half-angle.  For |x| <= 1/16 the Taylor series of sin and
-// cos truncated after x^11 / x^12 (remainder below 2^-60 relative) replaces
-// the library call; larger arguments use sincos.
-template <typename R> __device__ __forceinline__ void half_sincos(R x, R *s, R *c) {
-  if (fabs((double)x) <= 0.0625) {
+// sin x and cos x - 1.  For |x| <= 1/8 their Taylor series about 0,
+//   sin x     = x - x^3/3! + x^5/5! - ...,
+//   cos x - 1 = -x^2/2! + x^4/4! - x^6/6! + ...,
+// truncated where the first omitted term (the series alternate with
+// decreasing terms, so it bounds the remainder) is below half an ulp relative:
+// through x^9 / x^10 in FP64 (omitted terms 2.3e-17 and 3.9e-18 relative at
+// |x| = 1/8), through x^5 / x^6 in FP32 (7.6e-10, 1.9e-10).  cos x - 1 is
+// formed directly, so it keeps full relative precision for small x.  Larger
+// arguments use the half-angle identities cos x - 1 = -2 sin^2(x/2) and
+// sin x = 2 sin(x/2) cos(x/2) with the library sincos.
+template <typename R> __device__ __forceinline__ void sin_cosm1(R x, R *sn, R *cm1) {
+  if (fabs((double)x) <= 0.125) {
     const R x2 = x * x;
-    // sin x = x (1 - x^2/3! + x^4/5! - x^6/7! + x^8/9! - x^10/11!)
-    R ps = (R)(-1.0 / 39916800.0);
-    ps = ps * x2 + (R)(1.0 / 362880.0);
-    ps = ps * x2 + (R)(-1.0 / 5040.0);
-    ps = ps * x2 + (R)(1.0 / 120.0);
-    ps = ps * x2 + (R)(-1.0 / 6.0);
-    *s = x + x * (x2 * ps);
-    // cos x = 1 - x^2/2! + x^4/4! - x^6/6! + x^8/8! - x^10/10! + x^12/12!
-    R pc = (R)(1.0 / 479001600.0);
-    pc = pc * x2 + (R)(-1.0 / 3628800.0);
-    pc = pc * x2 + (R)(1.0 / 40320.0);
-    pc = pc * x2 + (R)(-1.0 / 720.0);
-    pc = pc * x2 + (R)(1.0 / 24.0);
-    pc = pc * x2 + (R)(-0.5);
-    *c = (R)1 + x2 * pc;
+    R ps, pc;
+    if (sizeof(R) == 8) {
+      ps = (R)(1.0 / 362880.0);
+      ps = ps * x2 + (R)(-1.0 / 5040.0);
+      ps = ps * x2 + (R)(1.0 / 120.0);
+      ps = ps * x2 + (R)(-1.0 / 6.0);
+      pc = (R)(-1.0 / 3628800.0);
+      pc = pc * x2 + (R)(1.0 / 40320.0);
+      pc = pc * x2 + (R)(-1.0 / 720.0);
+      pc = pc * x2 + (R)(1.0 / 24.0);
+      pc = pc * x2 + (R)(-0.5);
+    } else {
+      ps = (R)(1.0 / 120.0);
+      ps = ps * x2 + (R)(-1.0 / 6.0);
+      pc = (R)(-1.0 / 720.0);
+      pc = pc * x2 + (R)(1.0 / 24.0);
+      pc = pc * x2 + (R)(-0.5);
+    }
+    *sn = x + (x * x2) * ps;
+    *cm1 = x2 * pc;
   } else {
-    fsincos(x, s, c);
+    R s, c;
+    fsincos(x * (R)0.5, &s, &c);
+    *cm1 = (R)-2 * s * s;
+    *sn = (R)2 * s * c;
   }
 }
 
@@ -121,10 +136,8 @@ template <typename R> __device__ __forceinline__ cx<R> nonlinear_factor(cx<R> v,
     R f = fexpm1(-th);
     return mk<R>(v.x + v.x * f, v.y + v.y * f);
   }
-  R s, c;
-  half_sincos<R>(th * (R)0.5, &s, &c);
-  const R cm1 = (R)-2 * s * s;   // cos th - 1
-  const R sn = (R)2 * s * c;     // sin th
+  R sn, cm1;
+  sin_cosm1<R>(th, &sn, &cm1);
   // v (cm1 - i sn)
   return mk<R>(v.x + (v.x * cm1 + v.y * sn), v.y + (v.y * cm1 - v.x * sn));
 }
@@ -560,19 +573,27 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_pipe(CAr
 
 // ------------------------------------------ line-serial Crank-Nicolson
 // One thread per grid line, streaming the line through registers: the Thomas
-// algorithm in its textbook form (Sec. 2, the tridiagonal solve of each CN
-// half-step), with the right-hand side B psi formed on the fly,
+// elimination of the CN system A x = B psi of Sec. 2 (A = I + kt T, Dirichlet
+// ghosts), with the right-hand side formed on the fly,
 //   d_a  = psi_a + kt (psi_{a-1} - 2 psi_a + psi_{a+1}),
-//   d'_a = m_a (d_a + kt d'_{a-1}),        m_a = 1 / (1 + 2 kt - kt^2 m_{a-1}),
-//   x_a  = d'_a + (kt m_a) x_{a+1},
-// d' written over psi in place and read back by the same thread.  It executes
-// about half the arithmetic of the chunk-parallel solve (no scan, no
-// correction sweeps), which is what bounds the FP64 form: that form is limited
-// by the FP64 pipe, not by memory.  Neighbouring threads own neighbouring
-// lines, so a y or z sweep reads and writes one coalesced segment per warp and
-// step; an x sweep walks rows (every access of a warp hits 32 rows, each row's
-// 128-byte line staying in L1 for the next steps).  Loads run LS_K sites
-// ahead of the stores, from registers.  tab holds m (n values) then kt m (n).
+// and run from both ends of the line at once.  A has constant coefficients
+// and is persymmetric, so eliminating upwards from the last row has the same
+// pivots m_j = 1 / (1 + 2 kt - kt^2 m_{j-1}) counted from the end:
+//   top    (a = j = 0 .. k-1):      d'_a = m_j (d_a + kt d'_{a-1}),
+//   bottom (b = n-1-j, j < k-1):    e'_b = m_j (d_b + kt e'_{b+1}),
+//   middle row k = n/2:             x_k = mu (d_k + kt (d'_{k-1} + e'_{k+1})),
+//                                   mu = 1 / (1 + 2 kt - kt (alpha_{k-1} + alpha_{k-2})),
+//   back substitution outwards:     x_a = d'_a + alpha_j x_{a+1},  x_b = e'_b + alpha_j x_{b-1},
+// alpha_j = kt m_j.  The two halves are independent recurrences, which
+// doubles the arithmetic each thread has in flight (the FP64 pipe's latency,
+// not its throughput, limits a one-chain sweep at these occupancies), at the
+// operation count of the plain sweep: about half that of the chunk-parallel
+// solve.  d' and e' are written over psi and read back by the same thread.
+// Neighbouring threads own neighbouring lines, so a y or z sweep reads and
+// writes one coalesced segment per warp and step; an x sweep walks rows (each
+// row's 128-byte line stays in L1 for the next steps).  Loads run LS_K sites
+// ahead of the stores, from registers.  tab holds m (n values), alpha (n),
+// two chunk tables (2n, unused here) and mu.
 struct LArgs {
   void *psi;
   const void *tab;
@@ -586,22 +607,37 @@ struct LArgs {
   int n, ncols, final_pass, norm;
   double tau;
 };
-#define DGPE_LS_K 8
+#define DGPE_LS_K 4
 
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
-// kt v (+ w) for kt = tau (imaginary time, real Coef) or kt = i tau (real time)
+// Products with kt = tau (imaginary time, real Coef) or kt = i tau (real
+// time), written as FMAs:  fma: kt v + w;  rhs: (1 - 2 kt) c + kt s, the
+// Crank-Nicolson right-hand side B psi at a site with value c and neighbour
+// sum s;  cfma: a v + w for a table coefficient a.
 template <typename R, typename Coef> struct KtMul;
 template <typename R> struct KtMul<R, R> {
-  static __device__ __forceinline__ cx<R> mul(R tau, cx<R> v) { return mk<R>(tau * v.x, tau * v.y); }
   static __device__ __forceinline__ cx<R> fma(R tau, cx<R> v, cx<R> w) {
     return mk<R>(fma_r(tau, v.x, w.x), fma_r(tau, v.y, w.y));
   }
+  static __device__ __forceinline__ cx<R> rhs(R tau, R one_m2tau, cx<R> c, cx<R> s) {
+    return mk<R>(fma_r(tau, s.x, one_m2tau * c.x), fma_r(tau, s.y, one_m2tau * c.y));
+  }
+  static __device__ __forceinline__ cx<R> cfma(R a, cx<R> v, cx<R> w) {
+    return mk<R>(fma_r(a, v.x, w.x), fma_r(a, v.y, w.y));
+  }
 };
 template <typename R> struct KtMul<R, cx<R>> {
-  static __device__ __forceinline__ cx<R> mul(R tau, cx<R> v) { return mk<R>(-tau * v.y, tau * v.x); }
   static __device__ __forceinline__ cx<R> fma(R tau, cx<R> v, cx<R> w) {
     return mk<R>(fma_r(-tau, v.y, w.x), fma_r(tau, v.x, w.y));
+  }
+  // c + i tau (s - 2 c)
+  static __device__ __forceinline__ cx<R> rhs(R tau, R, cx<R> c, cx<R> s) {
+    const R t2 = tau + tau;
+    return mk<R>(fma_r(-tau, s.y, fma_r(t2, c.y, c.x)), fma_r(tau, s.x, fma_r(-t2, c.x, c.y)));
+  }
+  static __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> v, cx<R> w) {
+    return mk<R>(fma_r(a.x, v.x, fma_r(-a.y, v.y, w.x)), fma_r(a.x, v.y, fma_r(a.y, v.x, w.y)));
   }
 };
 
@@ -613,61 +649,96 @@ __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
   typedef KtMul<R, Coef> KT;
   constexpr int K = DGPE_LS_K;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = A.n;
+  const int n = A.n, k = n / 2;
   const long long es = A.es;
-  const R tau = (R)A.tau;
+  const R tau = (R)A.tau, one_m2tau = (R)(1.0 - 2.0 * A.tau);
   const Coef *tm = reinterpret_cast<const Coef *>(A.tab), *ta = tm + n;
   double acc = 0.0;
   if (c < A.ncols) {
     Cx *p = reinterpret_cast<Cx *>(A.psi) + (size_t)blockIdx.y * A.os + (size_t)c * A.cs;
-    // forward elimination; buf[i] holds psi_{a0 + 1 + i}
-    Cx buf[K], nb[K];
-    Cx prev = czero<Cx>(), cur = p[0], dp = czero<Cx>();
+    auto ld = [&](int a) { return p[(size_t)a * es]; };
+    auto nrm = [&](Cx v) { if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y; };
+    // forward elimination from both ends; for step j:
+    //   top row j, bt[i] = psi_{j+1};  bottom row n-1-j, bb[i] = psi_{n-2-j}
+    Cx bt[K], bb[K], nt[K], nb[K];
+    Cx prt = czero<Cx>(), cut = ld(0), dpt = czero<Cx>();
+    Cx prb = czero<Cx>(), cub = ld(n - 1), dpb = czero<Cx>();
 #pragma unroll
-    for (int i = 0; i < K; ++i) buf[i] = (1 + i < n) ? p[(size_t)(1 + i) * es] : czero<Cx>();
-    for (int a0 = 0; a0 < n; a0 += K) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const int j = a0 + K + 1 + i;
-        nb[i] = (j < n) ? p[(size_t)j * es] : czero<Cx>();
-      }
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const int a = a0 + i;
-        if (a < n) {
-          const Cx nxt = buf[i];
-          const Cx lap = (prev + nxt) - cur - cur;
-          const Cx d = KT::fma(tau, lap, cur);
-          dp = coef_mul(__ldg(tm + a), KT::fma(tau, dp, d));
-          p[(size_t)a * es] = dp;
-          prev = cur;
-          cur = nxt;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < K; ++i) buf[i] = nb[i];
+    for (int i = 0; i < K; ++i) {
+      bt[i] = (1 + i <= k) ? ld(1 + i) : czero<Cx>();
+      bb[i] = (n - 2 - i >= k) ? ld(n - 2 - i) : czero<Cx>();
     }
-    // back substitution; buf[i] holds d'_{a0 - i}
-    Cx x = czero<Cx>();
-#pragma unroll
-    for (int i = 0; i < K; ++i) buf[i] = (n - 1 - i >= 0) ? p[(size_t)(n - 1 - i) * es] : czero<Cx>();
-    for (int a0 = n - 1; a0 >= 0; a0 -= K) {
+    for (int j0 = 0; j0 < k; j0 += K) {
 #pragma unroll
       for (int i = 0; i < K; ++i) {
-        const int j = a0 - K - i;
-        nb[i] = (j >= 0) ? p[(size_t)j * es] : czero<Cx>();
+        const int jt = j0 + K + 1 + i, jb = n - 2 - (j0 + K + i);
+        nt[i] = (jt <= k) ? ld(jt) : czero<Cx>();
+        nb[i] = (jb >= k) ? ld(jb) : czero<Cx>();
       }
 #pragma unroll
       for (int i = 0; i < K; ++i) {
-        const int a = a0 - i;
-        if (a >= 0) {
-          x = buf[i] + coef_mul(__ldg(ta + a), x);
-          p[(size_t)a * es] = x;
-          if (A.norm) acc += (double)x.x * x.x + (double)x.y * x.y;
+        const int j = j0 + i;
+        if (j < k) {
+          const Coef mj = __ldg(tm + j);
+          {
+            const Cx nxt = bt[i];
+            const Cx d = KT::rhs(tau, one_m2tau, cut, prt + nxt);
+            dpt = coef_mul(mj, KT::fma(tau, dpt, d));
+            p[(size_t)j * es] = dpt;
+            prt = cut;
+            cut = nxt;
+          }
+          if (j < k - 1) {
+            const Cx nxt = bb[i];
+            const Cx d = KT::rhs(tau, one_m2tau, cub, prb + nxt);
+            dpb = coef_mul(mj, KT::fma(tau, dpb, d));
+            p[(size_t)(n - 1 - j) * es] = dpb;
+            prb = cub;
+            cub = nxt;
+          }
         }
       }
 #pragma unroll
-      for (int i = 0; i < K; ++i) buf[i] = nb[i];
+      for (int i = 0; i < K; ++i) { bt[i] = nt[i]; bb[i] = nb[i]; }
+    }
+    // middle row: cut = psi_k, prt = psi_{k-1}, prb = psi_{k+1}
+    const Cx dk = KT::rhs(tau, one_m2tau, cut, prt + prb);
+    const Cx xk = coef_mul(__ldg(tm + 4 * n), KT::fma(tau, dpt + dpb, dk));
+    p[(size_t)k * es] = xk;
+    nrm(xk);
+    // back substitution outwards; for step j (from k-1 down):
+    //   top row j, bt[i] = d'_j;  bottom row n-1-j (j <= k-2), bb[i] = e'_{n-1-j}
+    Cx xt = xk, xb = xk;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int j = k - 1 - i;
+      bt[i] = (j >= 0) ? ld(j) : czero<Cx>();
+      bb[i] = (j >= 0 && j <= k - 2) ? ld(n - 1 - j) : czero<Cx>();
+    }
+    for (int j0 = k - 1; j0 >= 0; j0 -= K) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = j0 - K - i;
+        nt[i] = (j >= 0) ? ld(j) : czero<Cx>();
+        nb[i] = (j >= 0 && j <= k - 2) ? ld(n - 1 - j) : czero<Cx>();
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = j0 - i;
+        if (j >= 0) {
+          const Coef aj = __ldg(ta + j);
+          xt = KT::cfma(aj, xt, bt[i]);
+          p[(size_t)j * es] = xt;
+          nrm(xt);
+          if (j <= k - 2) {
+            xb = KT::cfma(aj, xb, bb[i]);
+            p[(size_t)(n - 1 - j) * es] = xb;
+            nrm(xb);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) { bt[i] = nt[i]; bb[i] = nb[i]; }
     }
   }
   if (!A.final_pass) return;
