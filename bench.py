@@ -178,6 +178,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the cuFFT comparison step")
+    ap.add_argument("--cn", default="auto", choices=["auto", "serial", "chunked"],
+                    help="Crank-Nicolson solve form of the FP64 form (auto: the library's default "
+                         "for the grid size); the FP32 form always uses the chunk-parallel solve")
     ap.add_argument("--forms", default="both", choices=["both", "fp64", "fp32"],
                     help="precision forms to time (the first listed is the top-level line)")
     ap.add_argument("--prep-steps", type=int, default=None,
@@ -253,7 +256,7 @@ def main():
     for fp64 in order:
         name = "fp64" if fp64 else "fp32_bulk"
         S = dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, cn=None if (args.cn == "auto" or not fp64) else args.cn)
         S.set_psi(psi0)
         S.step(args.warmup)
         barrier()

@@ -401,7 +401,7 @@ template <typename R> struct EngineT : Engine {
       if (a == 0) { L.ncols = (int)nrows; L.es = 1; L.cs = nx; L.os = 0; }
       else if (a == 1) { L.ncols = nx; L.es = nx; L.cs = 1; L.os = (long long)nx * ny; }
       else { L.ncols = nx; L.es = (long long)nx * ny; L.cs = 1; L.os = nx; }
-      L.T = std::min(128, (L.ncols + 31) / 32 * 32);
+      L.T = std::min(DGPE_LINES_T, (L.ncols + 31) / 32 * 32);
       const unsigned outer = (a == 0) ? 1u : (a == 1 ? (unsigned)nz : (unsigned)ny);
       L.grid = dim3((unsigned)((L.ncols + L.T - 1) / L.T), outer);
     }

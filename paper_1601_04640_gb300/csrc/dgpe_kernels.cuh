@@ -162,6 +162,16 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 #define DGPE_MAXT 256
 #define DGPE_MINB(R) 2
 #define DGPE_MINB_FFT(R) (sizeof(R) == 4 ? 3 : 2)
+// FP32 blocks per SM the C2R/exponential/CN_x pass and the pipelined CN pass
+// are compiled for (register budget 65536 / (256 x this))
+#ifndef DGPE_MINB_P1_F32
+#define DGPE_MINB_P1_F32 3
+#endif
+#ifndef DGPE_MINB_CN_F32
+#define DGPE_MINB_CN_F32 2
+#endif
+#define DGPE_MINB_P1(R) (sizeof(R) == 4 ? DGPE_MINB_P1_F32 : 2)
+#define DGPE_MINB_CN(R) (sizeof(R) == 4 ? DGPE_MINB_CN_F32 : 2)
 
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
 template <typename R, int EPT, int SRC, bool POW2>
@@ -327,11 +337,11 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   }
 }
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_c2r_x_exp_cnx(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx(XArgs<R> A) {
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2>(A);
 }
 template <typename R, typename Coef, int EPT, int CL, bool POW2>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
   const XArgs<R> A = args[blockIdx.z];
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
 }
@@ -487,7 +497,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(co
 // the other shared buffer are in flight while the current tile is solved.
 // Tile id -> (column block id % nx_blocks, outer index id / nx_blocks).
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_pipe(CArgs<R> A, int ncb, int ntiles) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(CArgs<R> A, int ncb, int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ int am_last;
@@ -608,6 +618,9 @@ struct LArgs {
   double tau;
 };
 #define DGPE_LS_K 4
+#ifndef DGPE_LINES_T
+#define DGPE_LINES_T 64  // threads (lines) per block: 65536 lines make ~7 blocks per SM, an even single wave
+#endif
 
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
