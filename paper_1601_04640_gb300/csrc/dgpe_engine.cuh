@@ -790,10 +790,12 @@ template <typename R> struct EngineT : Engine {
     }
     return f;
   }
-  // exponential substep per site: scale (2), density (3), V (1), theta
-  // (5 with the dipolar term, else 3), the factor (real time: sin and
-  // cos - 1 by Taylor series, 19 in FP64 / 11 in FP32; imaginary time:
-  // expm1 counted as 1) and the increment update (8 real / 4 imaginary)
+  // exponential substep per site: V (1), theta (5 with the dipolar term,
+  // else 3), the factor (real time: sin and cos - 1 by Taylor series, 19 in
+  // FP64 / 11 in FP32; imaginary time: expm1 counted as 1) and the update:
+  // FP32 and imaginary time scale psi (2), form the density (3) and apply
+  // the factor in increment form (8 real / 4 imaginary); FP64 real time forms
+  // the scaled density (4), the scaled factor (3) and one complex product (6)
   double exp_flops_per_site() const {
     const double th = has_dip ? 5.0 : 3.0;
     if (imag) return 2 + 3 + 1 + th + 1 + 4;

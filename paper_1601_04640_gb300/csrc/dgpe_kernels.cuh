@@ -275,12 +275,26 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   const R gdddt = (R)(A.prm[PRM_DT] * A.prm[PRM_GDD]);
   const R sc = (R)A.prm[PRM_SC];
   const int imag = A.imag;
-  // exponential substep on the tile element (L, a) in place
+  // exponential substep on the tile element (L, a) in place.  FP64 real
+  // time multiplies the stored value by sc e^{-i theta} directly (the scale
+  // folded into the factor); FP32 forms the scaled value and updates it in
+  // increment form.
+  const R sc2 = sc * sc;
   auto apply_e = [&](int L, int a, R phi) {
     const int ia = L * P + a + a / CL;
+    const R V = A.vx[a] + s_vyz[L];
+    if (sizeof(R) == 8 && !imag) {
+      const cx<R> u = pt[ia];
+      const R dens = sc2 * (u.x * u.x + u.y * u.y);
+      const R th = dts * V + gdt * dens + gdddt * phi;
+      R sn, cm1;
+      sin_cosm1<R>(th, &sn, &cm1);
+      const R fr = sc + sc * cm1, fi = -sc * sn;  // sc (cos th - i sin th)
+      pt[ia] = mk<R>(u.x * fr - u.y * fi, u.x * fi + u.y * fr);
+      return;
+    }
     cx<R> v = cscale(pt[ia], sc);
     const R dens = v.x * v.x + v.y * v.y;
-    const R V = A.vx[a] + s_vyz[L];
     const R th = dts * V + gdt * dens + gdddt * phi;
     pt[ia] = nonlinear_factor<R>(v, th, imag);
   };
