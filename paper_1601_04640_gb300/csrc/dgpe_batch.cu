@@ -31,6 +31,7 @@ struct Cls {
   size_t xs = 0, x4s = 0, ss = 0, cs = 0;
   dim3 sgrid, cgrid;
   cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;  // join of the class's branch in the step graph
 };
 
 }  // namespace
@@ -42,6 +43,7 @@ struct dgpe_batch {
   std::vector<Eng *> eng;
   std::vector<Cls> cls;
   cudaStream_t stream = nullptr, cap = nullptr;
+  cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long sites = 0;
@@ -55,7 +57,9 @@ struct dgpe_batch {
       if (c.dS) cudaFree(c.dS);
       if (c.dC) cudaFree(c.dC);
       if (c.st) cudaStreamDestroy(c.st);
+      if (c.done) cudaEventDestroy(c.done);
     }
+    if (fork) cudaEventDestroy(fork);
     if (cap) cudaStreamDestroy(cap);
     for (Eng *e : eng) delete e;
   }
@@ -230,11 +234,21 @@ int autotune(dgpe_batch *b, Cls &c) {
   return set_attrs(b, c);
 }
 
+// One step of every class as one graph: the capture stream forks into one
+// branch per class (the class's own stream), the branches join back before
+// the capture ends, so the classes' kernels are free to run concurrently.
 int capture(dgpe_batch *b) {
   BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
   int rc = DGPE_OK;
-  for (auto &c : b->cls)
-    if ((rc = launch_class(b, c, b->cap))) break;
+  if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) rc = DGPE_ECUDA;
+  for (auto &c : b->cls) {
+    if (rc) break;
+    if (cudaStreamWaitEvent(c.st, b->fork, 0) != cudaSuccess) { rc = DGPE_ECUDA; break; }
+    if ((rc = launch_class(b, c, c.st))) break;
+    if (cudaEventRecord(c.done, c.st) != cudaSuccess || cudaStreamWaitEvent(b->cap, c.done, 0) != cudaSuccess)
+      rc = DGPE_ECUDA;
+  }
+  if (rc == DGPE_ECUDA) b->err = std::string("graph fork/join: ") + cudaGetErrorString(cudaGetLastError());
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -299,10 +313,12 @@ extern "C" int dgpe_batch_create(const dgpe_params *ps, int count, void *cuda_st
     b->cls[index[key]].members.push_back(i);
   }
   auto fail = [&](int rc) { g_batch_err = b->err; delete b; return rc; };
-  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) { b->err = "stream"; return fail(DGPE_ECUDA); }
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) { b->err = "stream"; return fail(DGPE_ECUDA); }
   for (auto &c : b->cls) {
     const size_t m = c.members.size();
     if (cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&c.dX, sizeof(XArgs<float>) * m) != cudaSuccess ||
         cudaMalloc(&c.dS, sizeof(SArgs<float>) * m) != cudaSuccess ||
         cudaMalloc(&c.dC, sizeof(CArgs<float>) * m) != cudaSuccess) {
