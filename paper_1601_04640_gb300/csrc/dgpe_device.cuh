@@ -434,6 +434,104 @@ __device__ __forceinline__ void stage_m_table(Coef *dst, const Coef *__restrict_
   for (int a = threadIdx.x; a < n; a += blockDim.x) dst[a + a / CL] = m[a];
 }
 
+// The same solve with the four tables m, alpha, P, Q read from a padded
+// shared copy (table k at tab + k TS, TS = n + n/CL + 1, coefficient a at
+// a + a/CL; see stage_cn_tables), for the FP32 bulk.  Every access is a
+// constant offset from the chunk's base (element a0 + i of the chunk sits at
+// base + i, a0 + CL at base + CL + 1, a0 - 1 at base - 2), the recurrences are
+// written as FMAs, and kt enters only through products with the real
+// (imaginary time) or purely imaginary (real time, make_kt gives (0, tau))
+// number kt, two multiplies each.
+__device__ __forceinline__ float2 kt_times(float kt, float2 v) { return make_float2(kt * v.x, kt * v.y); }
+__device__ __forceinline__ float2 kt_times(float2 kt, float2 v) { return make_float2(-kt.y * v.y, kt.y * v.x); }
+__device__ __forceinline__ double2 kt_times(double kt, double2 v) { return make_double2(kt * v.x, kt * v.y); }
+__device__ __forceinline__ double2 kt_times(double2 kt, double2 v) { return make_double2(-kt.y * v.y, kt.y * v.x); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+// a v + w for a real or complex coefficient a
+__device__ __forceinline__ float2 coef_fma(float a, float2 v, float2 w) {
+  return make_float2(fmaf(a, v.x, w.x), fmaf(a, v.y, w.y));
+}
+__device__ __forceinline__ float2 coef_fma(float2 a, float2 v, float2 w) {
+  return make_float2(fmaf(a.x, v.x, fmaf(-a.y, v.y, w.x)), fmaf(a.x, v.y, fmaf(a.y, v.x, w.y)));
+}
+__device__ __forceinline__ double2 coef_fma(double a, double2 v, double2 w) {
+  return make_double2(fma(a, v.x, w.x), fma(a, v.y, w.y));
+}
+__device__ __forceinline__ double2 coef_fma(double2 a, double2 v, double2 w) {
+  return make_double2(fma(a.x, v.x, fma(-a.y, v.y, w.x)), fma(a.x, v.y, fma(a.y, v.x, w.y)));
+}
+template <typename R, typename Coef, int CL>
+__device__ __forceinline__ void cn_line_st(cx<R> *line, int n, int TPL, int q, Coef kt,
+                                           const Coef *__restrict__ tab, bool active) {
+  typedef cx<R> Cx;
+  const int TS = n + n / CL + 1;
+  const int a0 = q * CL;
+  Cx *lp = line + a0 + q;                 // padded address of element a0
+  const Coef *tm = tab + a0 + q, *ta = tm + TS, *tp = ta + TS, *tq = tp + TS;
+  const Coef m2kt = coef_scale(kt, (R)(-2));
+  Cx y[CL];
+  Cx acc = czero<Cx>();
+  Cx prev = (active && a0 > 0) ? lp[-2] : czero<Cx>();
+  Cx cur = active ? lp[0] : czero<Cx>();
+#pragma unroll
+  for (int i = 0; i < CL; ++i) {
+    const int off = (i + 1 < CL) ? i + 1 : CL + 1;
+    const Cx nxt = (active && a0 + i + 1 < n) ? lp[off] : czero<Cx>();
+    // r = -2 kt (2 cur - prev - nxt)
+    const Cx s = prev + nxt;
+    const Cx r = kt_times(m2kt, mk<R>(fma_t((R)2, cur.x, -s.x), fma_t((R)2, cur.y, -s.y)));
+    const Coef ma = active ? tm[i] : coef_zero<Coef>();
+    const Coef al = active ? ta[i] : coef_zero<Coef>();
+    acc = coef_fma(al, acc, coef_mul(ma, r));
+    y[i] = acc;
+    prev = cur;
+    cur = nxt;
+  }
+  Coef P = active ? tp[CL - 1] : coef_zero<Coef>();
+  Cx Y = acc;
+  for (int d = 1; d < TPL; d <<= 1) {
+    Coef Pn = shfl_up(P, d, TPL);
+    Cx Yn = shfl_up(Y, d, TPL);
+    if (q >= d) { Y = coef_fma(P, Yn, Y); P = coef_prod(P, Pn); }
+  }
+  Cx yin = shfl_up(Y, 1, TPL);
+  if (q == 0) yin = czero<Cx>();
+#pragma unroll
+  for (int i = 0; i < CL; ++i) y[i] = coef_fma(active ? tp[i] : coef_zero<Coef>(), yin, y[i]);
+  acc = czero<Cx>();
+#pragma unroll
+  for (int i = CL - 1; i >= 0; --i) {
+    acc = coef_fma(active ? ta[i] : coef_zero<Coef>(), acc, y[i]);
+    y[i] = acc;
+  }
+  Coef Q = active ? tq[0] : coef_zero<Coef>();
+  Cx W = acc;
+  for (int d = 1; d < TPL; d <<= 1) {
+    Coef Qn = shfl_down(Q, d, TPL);
+    Cx Wn = shfl_down(W, d, TPL);
+    if (q + d < TPL) { W = coef_fma(Q, Wn, W); Q = coef_prod(Q, Qn); }
+  }
+  Cx win = shfl_down(W, 1, TPL);
+  if (q == TPL - 1) win = czero<Cx>();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < CL; ++i) lp[i] = lp[i] + coef_fma(tq[i], win, y[i]);
+  }
+}
+
+// Copy the four CN tables of an axis (m, alpha, P, Q; n each, in that order)
+// into shared memory in the padded layout cn_line_st reads.  All threads take
+// part; the caller synchronises before use.
+template <typename Coef, int CL>
+__device__ __forceinline__ void stage_cn_tables(Coef *dst, const Coef *__restrict__ tab, int n) {
+  const int TS = n + n / CL + 1;
+  for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) {
+    const int k = i / n, a = i - k * n;
+    dst[k * TS + a + a / CL] = tab[i];
+  }
+}
+
 // ------------------------------------------------ asynchronous tile copies
 // cp.async global -> shared copies (issued by every thread for its own
 // elements, completed per commit group) let a persistent CTA fetch its next

@@ -237,9 +237,10 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   __shared__ double s_dts;
   __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
   constexpr bool TAB = (sizeof(R) == 8);
-  // FP32: shared copy of the m table (the CN solve forms the rest in registers)
-  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
-  if (!TAB && MODE != 1 && MODE != 3) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), A.nx);
+  // FP32: padded shared copy of the four CN tables (FP64 reads them from
+  // global memory: its FP64 pipe, not the table loads, is the limit)
+  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
+  if (!TAB && MODE != 1 && MODE != 3) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), A.nx);
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
   const int ln = POW2 ? ilog2(n) : 0;
   const int p0 = blockIdx.x * A.LP;
@@ -339,8 +340,9 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // Crank-Nicolson along x: TPL lanes per line
   const int l = t / A.TPL, q = t - l * A.TPL;
   const bool active = (2 * p0 + l) < nrows;
-  cn_line<R, Coef, CL, TAB>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
-                            TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, active);
+  if constexpr (TAB) cn_line<R, Coef, CL, true>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                                      reinterpret_cast<const Coef *>(A.cntab), active);
+  else cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, active);
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
@@ -444,14 +446,15 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   }
   __syncthreads();
   constexpr bool TAB = (sizeof(R) == 8);
-  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
+  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
   if (!TAB) {
-    stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), n);
+    stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), n);
     __syncthreads();
   }
   const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-  cn_line<R, Coef, CL, TAB>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
-                            TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, c0 + l < A.ncols);
+  if constexpr (TAB) cn_line<R, Coef, CL, true>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                                      reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
+  else cn_line_st<R, Coef, CL>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
   __syncthreads();
   double acc = 0.0;
   if (c0 + lc < A.ncols) {
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
     cp_async_commit();
   };
   constexpr bool TAB = (sizeof(R) == 8);
-  __shared__ __align__(16) Coef s_m[TAB ? 1 : (512 + 512 / CL + 1)];
-  if (!TAB) stage_m_table<Coef, CL>(s_m, reinterpret_cast<const Coef *>(A.cntab), n);  // visible after the loop's first barrier
+  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
+  if (!TAB) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), n);  // visible after the loop's first barrier
   double acc = 0.0;
   int k = 0;
   if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, buf[0]);
@@ -549,8 +552,9 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
     const int c0 = cb * W;
     cx<R> *tb = buf[k];
     const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-    cn_line<R, Coef, CL, TAB>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
-                              TAB ? reinterpret_cast<const Coef *>(A.cntab) : s_m, c0 + l < A.ncols);
+    if constexpr (TAB) cn_line<R, Coef, CL, true>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+                                        reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
+    else cn_line_st<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
     __syncthreads();
     if (c0 + lc < A.ncols) {
       cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;
