@@ -58,11 +58,6 @@ __device__ __forceinline__ double coef_scale(double c, double s) { return c * s;
 __device__ __forceinline__ float coef_scale(float c, float s) { return c * s; }
 __device__ __forceinline__ double2 coef_scale(double2 c, double s) { return make_double2(c.x * s, c.y * s); }
 __device__ __forceinline__ float2 coef_scale(float2 c, float s) { return make_float2(c.x * s, c.y * s); }
-template <typename T> __device__ __forceinline__ T coef_one();
-template <> __device__ __forceinline__ double coef_one<double>() { return 1.0; }
-template <> __device__ __forceinline__ float coef_one<float>() { return 1.0f; }
-template <> __device__ __forceinline__ double2 coef_one<double2>() { return make_double2(1.0, 0.0); }
-template <> __device__ __forceinline__ float2 coef_one<float2>() { return make_float2(1.0f, 0.0f); }
 
 // warp shuffles within segments of `w` lanes
 __device__ __forceinline__ double shfl_up(double v, int d, int w) { return __shfl_up_sync(0xffffffffu, v, d, w); }
@@ -335,47 +330,36 @@ __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &p
 // per lane of a TPL-wide lane segment); chunk-local passes with zero inflow,
 // a Kogge-Stone scan of the chunk maps (P, Y) over the lanes, and a fix-up
 // with the in-chunk products P_a = prod_{b=a0..a} alpha_b and
-// Q_a = prod_{b=a..a0+CL-1} alpha_b.  With TABLES the kernel reads m, alpha,
-// P, Q (n each, in that order) from global memory; without, `tab` is a shared
-// copy of m in the padded layout below, and alpha, P, Q are formed in
-// registers (cheaper where arithmetic is plentiful).  The line lives in
+// Q_a = prod_{b=a..a0+CL-1} alpha_b.  This form (FP64) reads the tables m,
+// alpha, P, Q (n each, in that order) from global memory.  The line lives in
 // shared memory at line[a + a / CL] (one pad per chunk keeps the lanes'
 // accesses on distinct banks).
-template <typename R, typename Coef, int CL, bool TABLES>
+template <typename R, typename Coef, int CL>
 __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef kt,
                                         const Coef *__restrict__ tab, bool active) {
   typedef cx<R> Cx;
   const Coef *tm = tab, *ta = tab + n, *tp = tab + 2 * n, *tq = tab + 3 * n;
   const int a0 = q * CL;
   Cx y[CL];
-  Coef mm[CL];  // m_a of the chunk (the on-the-fly path forms alpha, P, Q from it)
   Cx acc = czero<Cx>();
   Cx prev = (active && a0 > 0) ? line[(a0 - 1) + (a0 - 1) / CL] : czero<Cx>();
   Cx cur = active ? line[a0 + a0 / CL] : czero<Cx>();
   const Coef m2kt = coef_scale(kt, (R)(-2));
-  Coef P = coef_one<Coef>();
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
     const int a = a0 + i;
     Cx nxt = (active && a + 1 < n) ? line[(a + 1) + (a + 1) / CL] : czero<Cx>();
     Cx lap = cur + cur - prev - nxt;
     Cx r = coef_mul(m2kt, lap);
-    const Coef ma = active ? (TABLES ? tm[a] : tm[a + a / CL]) : coef_zero<Coef>();
-    Coef al;
-    if (TABLES) {
-      al = active ? ta[a] : coef_zero<Coef>();
-    } else {
-      mm[i] = ma;
-      al = coef_prod(kt, ma);
-      P = coef_prod(P, al);
-    }
+    const Coef ma = active ? tm[a] : coef_zero<Coef>();
+    const Coef al = active ? ta[a] : coef_zero<Coef>();
     acc = coef_mul(al, acc) + coef_mul(ma, r);
     y[i] = acc;
     prev = cur;
     cur = nxt;
   }
   // inclusive scan over the chunks (lane segment of width TPL)
-  if (TABLES) P = active ? tp[a0 + CL - 1] : coef_zero<Coef>();
+  Coef P = active ? tp[a0 + CL - 1] : coef_zero<Coef>();
   Cx Y = acc;
   for (int d = 1; d < TPL; d <<= 1) {
     Coef Pn = shfl_up(P, d, TPL);
@@ -384,26 +368,20 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef
   }
   Cx yin = shfl_up(Y, 1, TPL);
   if (q == 0) yin = czero<Cx>();
-  Coef run = coef_one<Coef>();
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
-    Coef f;
-    if (TABLES) f = active ? tp[a0 + i] : coef_zero<Coef>();
-    else { run = coef_prod(run, coef_prod(kt, mm[i])); f = run; }
+    const Coef f = active ? tp[a0 + i] : coef_zero<Coef>();
     y[i] = y[i] + coef_mul(f, yin);
   }
   // chunk-local backward recurrence
   acc = czero<Cx>();
-  Coef Q = coef_one<Coef>();
 #pragma unroll
   for (int i = CL - 1; i >= 0; --i) {
-    Coef al;
-    if (TABLES) al = active ? ta[a0 + i] : coef_zero<Coef>();
-    else { al = coef_prod(kt, mm[i]); Q = coef_prod(Q, al); }
+    const Coef al = active ? ta[a0 + i] : coef_zero<Coef>();
     acc = y[i] + coef_mul(al, acc);
     y[i] = acc;
   }
-  if (TABLES) Q = active ? tq[a0] : coef_zero<Coef>();
+  Coef Q = active ? tq[a0] : coef_zero<Coef>();
   Cx W = acc;
   for (int d = 1; d < TPL; d <<= 1) {
     Coef Qn = shfl_down(Q, d, TPL);
@@ -412,26 +390,15 @@ __device__ __forceinline__ void cn_line(cx<R> *line, int n, int TPL, int q, Coef
   }
   Cx win = shfl_down(W, 1, TPL);
   if (q == TPL - 1) win = czero<Cx>();
-  run = coef_one<Coef>();
   if (active) {
 #pragma unroll
     for (int i = CL - 1; i >= 0; --i) {
       const int a = a0 + i;
-      Coef f;
-      if (TABLES) f = tq[a];
-      else { run = coef_prod(run, coef_prod(kt, mm[i])); f = run; }
-      Cx w = y[i] + coef_mul(f, win);
+      Cx w = y[i] + coef_mul(tq[a], win);
       const int ia = a + a / CL;
       line[ia] = line[ia] + w;
     }
   }
-}
-
-// Copy the m table of an axis (n coefficients) into shared memory in the
-// padded layout cn_line reads (index a + a / CL).  All threads take part.
-template <typename Coef, int CL>
-__device__ __forceinline__ void stage_m_table(Coef *dst, const Coef *__restrict__ m, int n) {
-  for (int a = threadIdx.x; a < n; a += blockDim.x) dst[a + a / CL] = m[a];
 }
 
 // The same solve with the four tables m, alpha, P, Q read from a padded

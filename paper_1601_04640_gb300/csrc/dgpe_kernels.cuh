@@ -340,7 +340,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // Crank-Nicolson along x: TPL lanes per line
   const int l = t / A.TPL, q = t - l * A.TPL;
   const bool active = (2 * p0 + l) < nrows;
-  if constexpr (TAB) cn_line<R, Coef, CL, true>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+  if constexpr (TAB) cn_line<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), active);
   else cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, active);
   __syncthreads();
@@ -452,7 +452,7 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
     __syncthreads();
   }
   const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-  if constexpr (TAB) cn_line<R, Coef, CL, true>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+  if constexpr (TAB) cn_line<R, Coef, CL>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
   else cn_line_st<R, Coef, CL>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
   __syncthreads();
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
     const int c0 = cb * W;
     cx<R> *tb = buf[k];
     const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-    if constexpr (TAB) cn_line<R, Coef, CL, true>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+    if constexpr (TAB) cn_line<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
                                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
     else cn_line_st<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
     __syncthreads();
