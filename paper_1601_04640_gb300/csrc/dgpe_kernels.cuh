@@ -157,13 +157,17 @@ __device__ __forceinline__ double trap_dts(const double *prm, long long step) {
 template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx<R>); };
 
 // Every pass is launched with at most DGPE_MAXT threads per block and held to
-// 2 resident blocks per SM worth of registers (128 per thread); the FP32
-// strided transforms to 3 (about 85), which measured faster for them.
+// 2 resident blocks per SM worth of registers (128 per thread), except these
+// FP32 kernels, whose register budgets (65536 / (256 x blocks)) were picked by
+// timing the 256^3 step: strided transforms 4 blocks (64 registers; 3 blocks
+// made FFT_z.U.IFFT_z 11 % slower), C2R/exponential/CN_x 3 blocks (2: 7 %
+// slower, 4: 13 % slower), pipelined CN 2 blocks (3: 14 % slower).
 #define DGPE_MAXT 256
 #define DGPE_MINB(R) 2
-#define DGPE_MINB_FFT(R) (sizeof(R) == 4 ? 3 : 2)
-// FP32 blocks per SM the C2R/exponential/CN_x pass and the pipelined CN pass
-// are compiled for (register budget 65536 / (256 x this))
+#ifndef DGPE_MINB_FFT_F32
+#define DGPE_MINB_FFT_F32 4
+#endif
+#define DGPE_MINB_FFT(R) (sizeof(R) == 4 ? DGPE_MINB_FFT_F32 : 2)
 #ifndef DGPE_MINB_P1_F32
 #define DGPE_MINB_P1_F32 3
 #endif
