@@ -790,16 +790,18 @@ template <typename R> struct EngineT : Engine {
     }
     return f;
   }
-  // exponential substep per site: V (1), theta (5 with the dipolar term,
-  // else 3), the factor (real time: sin and cos - 1 by Taylor series, 19 in
-  // FP64 / 11 in FP32; imaginary time: expm1 counted as 1) and the update:
-  // FP32 and imaginary time scale psi (2), form the density (3) and apply
-  // the factor in increment form (8 real / 4 imaginary); FP64 real time forms
-  // the scaled density (4), the scaled factor (3) and one complex product (6)
+  // exponential substep per site.  FP32 and imaginary time: V (1), scaled
+  // psi (2), density (3), theta (5 with the dipolar term, else 3), the factor
+  // (real time: sin and cos - 1 by Taylor series, 11 in FP32; imaginary time:
+  // expm1 counted as 1) and its increment-form update (8 real / 4 imaginary).
+  // FP64 real time: theta from |psi|^2 and the dt-scaled potentials (8 with
+  // the dipolar term, else 6), sin and cos - 1 (19), the scaled factor (3)
+  // and one complex product (6).
   double exp_flops_per_site() const {
+    if (sizeof(R) == 8 && !imag) return (has_dip ? 8.0 : 6.0) + 19.0 + 3.0 + 6.0;
     const double th = has_dip ? 5.0 : 3.0;
-    if (imag) return 2 + 3 + 1 + th + 1 + 4;
-    return 2 + 3 + 1 + th + (sizeof(R) == 8 ? 19.0 : 11.0) + 8;
+    if (imag) return 1 + 2 + 3 + th + 1 + 4;
+    return 1 + 2 + 3 + th + 11.0 + 8;
   }
   // Thomas solve per site: line-serial (forward right-hand side, forward
   // elimination, back substitution) or chunk-parallel (chunk passes, the two

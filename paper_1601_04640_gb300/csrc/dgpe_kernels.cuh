@@ -241,6 +241,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   __shared__ double s_dts;
   __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
   constexpr bool TAB = (sizeof(R) == 8);
+  __shared__ R s_dvx[TAB ? 512 : 1];  // FP64 real time: dt s(t) V_x
   // FP32: padded shared copy of the four CN tables (FP64 reads them from
   // global memory: its FP64 pipe, not the table loads, is the limit)
   __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
@@ -280,24 +281,30 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   const R gdddt = (R)(A.prm[PRM_DT] * A.prm[PRM_GDD]);
   const R sc = (R)A.prm[PRM_SC];
   const int imag = A.imag;
+  constexpr bool DIRECT = (sizeof(R) == 8);  // FP64: the direct (scaled) phase factor in real time
+  if (DIRECT && !imag && MODE != 1 && MODE != 2) {
+    // dt s(t) V with the scale of V_y + V_z applied in place (each CTA owns its rows)
+    for (int a = t; a < n; a += T) s_dvx[a] = dts * A.vx[a];
+    if (t < 2 * A.LP) s_vyz[t] *= dts;
+    __syncthreads();
+  }
   // exponential substep on the tile element (L, a) in place.  FP64 real
   // time multiplies the stored value by sc e^{-i theta} directly (the scale
   // folded into the factor); FP32 forms the scaled value and updates it in
   // increment form.
-  const R sc2 = sc * sc;
+  const R gdt_sc2 = gdt * sc * sc;
   auto apply_e = [&](int L, int a, R phi) {
     const int ia = L * P + a + a / CL;
-    const R V = A.vx[a] + s_vyz[L];
-    if (sizeof(R) == 8 && !imag) {
+    if (DIRECT && !imag) {
       const cx<R> u = pt[ia];
-      const R dens = sc2 * (u.x * u.x + u.y * u.y);
-      const R th = dts * V + gdt * dens + gdddt * phi;
+      const R th = gdt_sc2 * (u.x * u.x + u.y * u.y) + (gdddt * phi + (s_dvx[a] + s_vyz[L]));
       R sn, cm1;
       sin_cosm1<R>(th, &sn, &cm1);
       const R fr = sc + sc * cm1, fi = -sc * sn;  // sc (cos th - i sin th)
       pt[ia] = mk<R>(u.x * fr - u.y * fi, u.x * fi + u.y * fr);
       return;
     }
+    const R V = A.vx[a] + s_vyz[L];
     cx<R> v = cscale(pt[ia], sc);
     const R dens = v.x * v.x + v.y * v.y;
     const R th = dts * V + gdt * dens + gdddt * phi;
