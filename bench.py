@@ -264,9 +264,11 @@ def main():
         clk.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        l0 = dgpe.dgpe_kernel_launches(S.h)
         e0.record(stream)
         S.step(args.steps)
         e1.record(stream)
+        launches = dgpe.dgpe_kernel_launches(S.h) - l0
         barrier()
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
@@ -277,7 +279,6 @@ def main():
         obs = S.observables()
         # per-pass durations (passes launched one by one, events between them)
         passes = dgpe.dgpe_profile_steps(S.h, max(3, args.steps // 2))
-        launches = dgpe.dgpe_launches_per_step(S.h) * args.steps
         tot = sum(p[1] for p in passes)
         top = max(passes, key=lambda p: p[1])
         achieved = top[2] / (top[1] * 1e-3) / 1e9
@@ -529,18 +530,20 @@ def bench_adjoint(args, wl, world, rank, local):
             s.set_trap_modulation(cm)
             dgpe.dgpe_fidelity_gradient(s.h, psi0, target, 2 * every, every, len(cm))  # warm-up
             torch.cuda.synchronize()
+            l0 = dgpe.dgpe_kernel_launches(s.h)
             t0 = time.perf_counter()
             F, dg, dc = dgpe.dgpe_fidelity_gradient(s.h, psi0, target, Kf, every, len(cm))
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+            nl = dgpe.dgpe_kernel_launches(s.h) - l0
         sites = n[0] * n[1] * n[2]
         out["fp64" if fp64 else "fp32_bulk"] = {"steps": Kf, "seconds": dt, "value": sites * Kf / dt,
-                                                 "F": F, "dF_dg": dg, "dF_dc": dc}
+                                                 "F": F, "dF_dg": dg, "dF_dc": dc, "gpu_launches": nl}
     a = out["fp32_bulk"]
     line = _peak_line("adjoint: forward+reverse site-updates/s of one fidelity gradient", a["value"],
                       "site-updates/s", a["steps"], 1, 1e3 * a["seconds"] / a["steps"],
                       "f32 (FP64 reductions/tables)", {"workload": wl["desc"], "grid": list(n)}, 1,
-                      forms=out, gpu_launches=None)
+                      forms=out, gpu_launches=a["gpu_launches"])
     print(json.dumps(line))
 
 

@@ -175,6 +175,11 @@ double dgpe_pass_bytes(dgpe_t h, int i);
  * recurrences).  0 for an index out of range or a NULL handle. */
 double dgpe_pass_flops(dgpe_t h, int i);
 
+/* Kernels this handle has launched since it was created (each replay of the
+ * step graph counts the step's kernels; observables, copies in and out and
+ * the adjoint calls count theirs).  0 for a NULL handle. */
+long long dgpe_kernel_launches(dgpe_t h);
+
 /* Reverse mode of one real-time step (the adjoint form: Wirtinger
  * convention G = 2 dL/dpsi*).  psi_in: device state at the start of step
  * `step` (complex128 for DGPE_FP64, complex64 for DGPE_FP32_BULK); G: device

@@ -188,6 +188,7 @@ extern "C" const char *dgpe_pass_name(dgpe_t h, int i) { return h ? h->eng->pass
 
 extern "C" double dgpe_pass_bytes(dgpe_t h, int i) { return h ? h->eng->pass_bytes(i) : 0.0; }
 extern "C" double dgpe_pass_flops(dgpe_t h, int i) { return h ? h->eng->pass_flops(i) : 0.0; }
+extern "C" long long dgpe_kernel_launches(dgpe_t h) { return h ? h->eng->kernel_launches() : 0; }
 
 extern "C" int dgpe_step_adjoint(dgpe_t h, const void *psi_in, void *G, long long step, double *dL_dg,
                                  double *dL_dc) {

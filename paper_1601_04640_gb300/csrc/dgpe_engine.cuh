@@ -44,6 +44,7 @@ struct Engine {
   virtual const char *pass_name(int i) const = 0;
   virtual double pass_bytes(int i) const = 0;
   virtual double pass_flops(int i) const = 0;
+  virtual long long kernel_launches() const = 0;
   virtual size_t sites() const = 0;
   std::string err;
 };
@@ -206,6 +207,12 @@ template <typename R> struct EngineT : Engine {
   struct LnCfg { int n, ncols, T; long long es, cs, os; dim3 grid; };
   LnCfg ln[3];
   bool cn_serial = false;
+  // kernels this solver has launched (a graph replay counts its kernels;
+  // launches recorded into a capture are not counted)
+  long long nlaunch = 0;
+  bool capturing = false;
+  void launched(int k) { if (!capturing) nlaunch += k; }
+  long long kernel_launches() const override { return nlaunch; }
   struct FtCfg { int n, T, W; long long es, os; dim3 grid; size_t smem; FftPlan pl; int axis; };
   FtCfg fy{}, fz{};
   int obs_rows = 1, obs_blocks = 0, ndip = 0;
@@ -618,6 +625,7 @@ template <typename R> struct EngineT : Engine {
       }
       return DGPE_OK;
     });
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -637,6 +645,7 @@ template <typename R> struct EngineT : Engine {
       else k_cn_strided_pipe<R, Cx, CL><<<c.pgrid[1], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
       return DGPE_OK;
     });
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -650,6 +659,7 @@ template <typename R> struct EngineT : Engine {
     A.tau = adjoint ? -tau[axis] : tau[axis];
     if (imag) k_cn_lines<R, R><<<L.grid, L.T, 0, s>>>(A);
     else k_cn_lines<R, Cx><<<L.grid, L.T, 0, s>>>(A);
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -665,6 +675,7 @@ template <typename R> struct EngineT : Engine {
       else k_dens_r2c_x<R, EX, 0, P2><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -694,6 +705,7 @@ template <typename R> struct EngineT : Engine {
       }
       return DGPE_OK;
     });
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -864,7 +876,9 @@ template <typename R> struct EngineT : Engine {
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
     if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     DGPE_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
     int rc = launch_step(cap);
+    capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -877,7 +891,10 @@ template <typename R> struct EngineT : Engine {
   // ------------------------------------------------------------ API calls
   int step(int n, cudaStream_t s) override {
     for (int i = 0; i < n; ++i) {
-      if (use_graph) DGPE_CK(cudaGraphLaunch(gexec, s));
+      if (use_graph) {
+        DGPE_CK(cudaGraphLaunch(gexec, s));
+        nlaunch += launches_per_step();
+      }
       else {
         int rc = launch_step(s);
         if (rc) return rc;
@@ -909,6 +926,7 @@ template <typename R> struct EngineT : Engine {
     const int blocks = 152 * 8;
     if (fp64) k_import<R, double2><<<blocks, 256, 0, s>>>(psi, (const double2 *)src, nsites);
     else k_import<R, float2><<<blocks, 256, 0, s>>>(psi, (const float2 *)src, nsites);
+    launched(1);
     DGPE_LCK(__func__);
     int rc = reset_scale(s);
     if (rc) return rc;
@@ -918,6 +936,7 @@ template <typename R> struct EngineT : Engine {
     const int blocks = 152 * 8;
     if (fp64) k_export<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, psi, prm, nsites);
     else k_export<R, float2><<<blocks, 256, 0, s>>>((float2 *)dst, psi, prm, nsites);
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -940,8 +959,10 @@ template <typename R> struct EngineT : Engine {
     A.rows_per_block = 0; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
     A.nux = p.nu[0]; A.nuy = p.nu[1]; A.nuz = (dim == 3) ? p.nu[2] : 0.0;
     k_obs_sites<R><<<obs_blocks, 256, 0, s>>>(A);
+    launched(1);
     DGPE_LCK("site sums");
     k_obs_final<<<1, 256, 0, s>>>(obs_part, obs_blocks, dip_part, ndip, obs_out);
+    launched(1);
     DGPE_LCK("final sums");
     double h[OBS_COUNT + 1];
     double hp[PRM_COUNT];
@@ -1002,6 +1023,7 @@ template <typename R> struct EngineT : Engine {
     if (mode != DGPE_IMAG && mode != DGPE_REAL) { err = "bad mode"; return DGPE_EINVAL; }
     // fold the lazy scale into psi, then rebuild the CN tables and the graph
     k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, nsites);
+    launched(1);
     DGPE_LCK(__func__);
     int rc = reset_scale(s);
     if (rc) return rc;
@@ -1059,6 +1081,7 @@ template <typename R> struct EngineT : Engine {
     const int nblk = 152 * 8;
     k_adj_sigma<R><<<nblk, 256, 0, s>>>(A);
     k_adj_accumulate<<<1, 256, 0, s>>>(adj_part, nblk, adj_acc, p.dt, t, host_M);
+    launched(2);
     DGPE_LCK(__func__);
     if (has_dip) {
       if ((rc = launch_dipolar_chain(s, nullptr, adj_sig))) return rc;
@@ -1067,6 +1090,7 @@ template <typename R> struct EngineT : Engine {
       DGPE_CK(cudaMemsetAsync(adj_ksig, 0, sizeof(R) * nsites, s));
     }
     k_adj_update<R><<<nblk, 256, 0, s>>>(A);
+    launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
@@ -1109,6 +1133,7 @@ template <typename R> struct EngineT : Engine {
     // c = h^d sum conj(target) psi_T, F = |c|^2, G_T = 2 h^d c target
     const int nblk = 152 * 8;
     k_cdot<R><<<nblk, 256, 0, s>>>(adjT, psi, nsites, adj_part);
+    launched(1);
     DGPE_LCK(__func__);
     std::vector<double> part(2 * nblk);
     DGPE_CK(cudaMemcpyAsync(part.data(), adj_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
@@ -1119,6 +1144,7 @@ template <typename R> struct EngineT : Engine {
     cr *= cell; ci *= cell;
     *F = cr * cr + ci * ci;
     k_cscale<R><<<nblk, 256, 0, s>>>(adjG, adjT, 2.0 * cell * cr, 2.0 * cell * ci, nsites);
+    launched(1);
     DGPE_CK(cudaMemsetAsync(adj_acc, 0, 17 * sizeof(double), s));
     // reverse sweep
     for (int j = nseg - 1; j >= 0; --j) {

@@ -41,7 +41,7 @@ EXPORTS = [
     "dgpe_get_psi_device", "dgpe_step", "dgpe_observables", "dgpe_dipolar_potential",
     "dgpe_set_g", "dgpe_set_mode", "dgpe_set_trap_modulation", "dgpe_set_time",
     "dgpe_get_time", "dgpe_sync", "dgpe_launches_per_step", "dgpe_last_error",
-    "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes", "dgpe_pass_flops",
+    "dgpe_profile_steps", "dgpe_pass_name", "dgpe_pass_bytes", "dgpe_pass_flops", "dgpe_kernel_launches",
     "dgpe_dipolar_potential_noalloc", "dgpe_noalloc_last_error",
     "dgpe_step_adjoint", "dgpe_fidelity_gradient",
     "dgpe_batch_create", "dgpe_batch_destroy", "dgpe_batch_set_psi", "dgpe_batch_get_psi",
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
         lib.dgpe_pass_bytes.restype = C.c_double
         lib.dgpe_pass_flops.argtypes = [H, C.c_int]
         lib.dgpe_pass_flops.restype = C.c_double
+        lib.dgpe_kernel_launches.argtypes = [H]
+        lib.dgpe_kernel_launches.restype = C.c_longlong
         lib.dgpe_dipolar_potential_noalloc.argtypes = [
             C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
             C.c_int, C.c_double, C.c_void_p]
@@ -234,6 +236,10 @@ def dgpe_sync(h):
 
 def dgpe_launches_per_step(h):
     return load().dgpe_launches_per_step(h)
+
+
+def dgpe_kernel_launches(h):
+    return load().dgpe_kernel_launches(h)
 
 
 def dgpe_profile_steps(h, n):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared(header="dgpe.h"):
     src = open(os.path.join(ROOT, "include", header)).read()
-    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dgpe_\w+)\s*\(", src, re.M))
+    return set(re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)*?\w+\s*\*?\s*(dgpe_\w+)\s*\(", src, re.M))
 
 
 def test_every_header_is_checked():

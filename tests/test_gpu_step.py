@@ -327,3 +327,26 @@ def test_device_pointer_roundtrip():
             assert np.max(np.abs(out.cpu().numpy() - psi0)) <= (0 if fp64 else 1e-7)
             host = s.get_psi()
             assert np.array_equal(host, out.cpu().numpy())
+
+
+def test_launch_counter_and_operation_model():
+    """dgpe_kernel_launches counts a graph replay as the step's kernels and the
+    observables' own kernels; dgpe_pass_flops gives the line-serial Thomas
+    solve 28 flops per site in real time (FP64)."""
+    n, h, nu = (64, 64, 64), (0.2,) * 3, (1.0, 1.0, 0.5)
+    with dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, False, True, cn="serial") as s:
+        s.set_psi(synth.gaussian_state(n, h, (1.0, 1.0, 0.5), 0.01, 3))
+        lps = dgpe.dgpe_launches_per_step(s.h)
+        l0 = dgpe.dgpe_kernel_launches(s.h)
+        s.step(3)
+        assert dgpe.dgpe_kernel_launches(s.h) - l0 == 3 * lps
+        l1 = dgpe.dgpe_kernel_launches(s.h)
+        s.observables()
+        assert dgpe.dgpe_kernel_launches(s.h) - l1 >= 2
+        lib = dgpe.load()
+        names = [lib.dgpe_pass_name(s.h, i).decode() for i in range(lps)]
+        flops = [lib.dgpe_pass_flops(s.h, i) for i in range(lps)]
+        assert names[-3:] == ["cn_x", "cn_y", "cn_z"]
+        for f in flops[-3:]:
+            assert f == 28.0 * 64 ** 3
+        assert all(f > 0 for f in flops)
