@@ -351,8 +351,8 @@ template <typename R> struct EngineT : Engine {
       // tile width W columns (128 B rows), narrowed (by powers of two) so
       // blocks stay <= DGPE_MAXT threads
       auto wfor = [&](int n, int ept) {
-        int w = W;
-        while (w > 1 && w * n / ept > DGPE_MAXT) w >>= 1;
+        int w = (sizeof(R) == 4) ? DGPE_W_FFT_F32 : W;
+        while (w > 1 && w * n / ept > DGPE_MAXT_FFT) w >>= 1;
         return w;
       };
       const int ey = variant_ept_s(var[1], EPT_S);
@@ -363,7 +363,7 @@ template <typename R> struct EngineT : Engine {
         fz.n = nz; fz.W = wfor(nz, ez); fz.T = fz.W * nz / ez; fz.es = (long long)ny * px; fz.os = px;
         fz.grid = dim3((ncol_spec + fz.W - 1) / fz.W, ny); fz.smem = sizeof(Cx) * (size_t)nz * fz.W; fz.pl = plz;
       }
-      if (fy.T > DGPE_MAXT || fz.T > DGPE_MAXT) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
+      if (fy.T > DGPE_MAXT_FFT || fz.T > DGPE_MAXT_FFT) { err = "strided FFT block too large"; return DGPE_EUNSUPPORTED; }
     }
     // scratch: norm partials, observable partials
     obs_blocks = (int)std::min<size_t>(152 * 8, (nsites + 255) / 256);
@@ -657,8 +657,9 @@ template <typename R> struct EngineT : Engine {
     A.es = L.es; A.cs = L.cs; A.os = L.os; A.n = L.n; A.ncols = L.ncols;
     A.final_pass = final_pass ? 1 : 0; A.norm = (final_pass && imag) ? 1 : 0;
     A.tau = adjoint ? -tau[axis] : tau[axis];
-    if (imag) k_cn_lines<R, R><<<L.grid, L.T, 0, s>>>(A);
-    else k_cn_lines<R, Cx><<<L.grid, L.T, 0, s>>>(A);
+    if (imag && A.norm) k_cn_lines<R, R, true><<<L.grid, L.T, 0, s>>>(A);
+    else if (imag) k_cn_lines<R, R, false><<<L.grid, L.T, 0, s>>>(A);
+    else k_cn_lines<R, Cx, false><<<L.grid, L.T, 0, s>>>(A);
     launched(1);
     DGPE_LCK(__func__);
     return DGPE_OK;

@@ -163,6 +163,12 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 // made FFT_z.U.IFFT_z 11 % slower), C2R/exponential/CN_x 3 blocks (2: 7 %
 // slower, 4: 13 % slower), pipelined CN 2 blocks (3: 14 % slower).
 #define DGPE_MAXT 256
+#ifndef DGPE_MAXT_FFT
+#define DGPE_MAXT_FFT 256  // strided transforms
+#endif
+#ifndef DGPE_W_FFT_F32
+#define DGPE_W_FFT_F32 16  // FP32 strided transforms: columns per tile
+#endif
 #define DGPE_MINB(R) 2
 #ifndef DGPE_MINB_FFT_F32
 #define DGPE_MINB_FFT_F32 4
@@ -419,11 +425,11 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   }
 }
 template <typename R, int EPT, int MODE, bool POW2 = true>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_FFT(R)) k_fft_strided(SArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R)) k_fft_strided(SArgs<R> A) {
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
 template <typename R, int EPT, int MODE, bool POW2>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_FFT(R)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
   const SArgs<R> A = args[blockIdx.z];
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
@@ -673,9 +679,8 @@ template <typename R> struct KtMul<R, cx<R>> {
   static __device__ __forceinline__ cx<R> fma(R tau, cx<R> v, cx<R> w) {
     return mk<R>(fma_r(-tau, v.y, w.x), fma_r(tau, v.x, w.y));
   }
-  // c + i tau (s - 2 c)
-  static __device__ __forceinline__ cx<R> rhs(R tau, R, cx<R> c, cx<R> s) {
-    const R t2 = tau + tau;
+  // c + i tau (s - 2 c); t2 = 2 tau
+  static __device__ __forceinline__ cx<R> rhs(R tau, R t2, cx<R> c, cx<R> s) {
     return mk<R>(fma_r(-tau, s.y, fma_r(t2, c.y, c.x)), fma_r(tau, s.x, fma_r(-t2, c.x, c.y)));
   }
   static __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> v, cx<R> w) {
@@ -683,7 +688,9 @@ template <typename R> struct KtMul<R, cx<R>> {
   }
 };
 
-template <typename R, typename Coef>
+// NORM: accumulate the FP64 norm (the final pass of an imaginary-time step);
+// a template flag so that the real-time passes carry no norm arithmetic.
+template <typename R, typename Coef, bool NORM>
 __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
   __shared__ double red[32];
   __shared__ int am_last;
@@ -693,13 +700,17 @@ __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = A.n, k = n / 2;
   const long long es = A.es;
-  const R tau = (R)A.tau, one_m2tau = (R)(1.0 - 2.0 * A.tau);
+  // second constant of KT::rhs: 1 - 2 tau (real kt) or 2 tau (imaginary kt)
+  const R tau = (R)A.tau;
+  const R one_m2tau = (sizeof(Coef) == sizeof(R)) ? (R)(1.0 - 2.0 * A.tau) : (R)(2.0 * A.tau);
   const Coef *tm = reinterpret_cast<const Coef *>(A.tab), *ta = tm + n;
   double acc = 0.0;
   if (c < A.ncols) {
     Cx *p = reinterpret_cast<Cx *>(A.psi) + (size_t)blockIdx.y * A.os + (size_t)c * A.cs;
     auto ld = [&](int a) { return p[(size_t)a * es]; };
-    auto nrm = [&](Cx v) { if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y; };
+    auto nrm = [&](Cx v) {
+      if constexpr (NORM) acc += (double)v.x * v.x + (double)v.y * v.y;
+    };
     // forward elimination from both ends; for step j:
     //   top row j, bt[i] = psi_{j+1};  bottom row n-1-j, bb[i] = psi_{n-2-j}
     Cx bt[K], bb[K], nt[K], nb[K];
@@ -787,7 +798,7 @@ __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
   const int t = threadIdx.x, T = blockDim.x;
   const unsigned nblk = gridDim.x * gridDim.y;
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (A.norm) {
+  if (NORM) {
     const double sblk = block_sum(acc, red);
     if (t == 0) A.partial[bid] = sblk;
   }
@@ -799,7 +810,7 @@ __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  if (A.norm) {
+  if (NORM) {
     double sum = 0.0;
     for (unsigned i = t; i < nblk; i += T) sum += __ldcg(A.partial + i);
     sum = block_sum(sum, red);
