@@ -114,7 +114,7 @@ class Clocks:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
 
@@ -171,7 +171,7 @@ def run_oracle_sample(wl, seconds=12.0, max_steps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="real3d", choices=sorted(WORKLOADS))
@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--prep-steps", type=int, default=None,
                     help="imaginary-time preparation steps (default: the workload's)")
     args = ap.parse_args()
+    args.steps_default = "--steps" not in " ".join(sys.argv[1:])
     wl = dict(WORKLOADS[args.workload])
     if args.prep_steps is not None:
         wl["prep_steps"] = args.prep_steps
@@ -518,7 +519,7 @@ def bench_adjoint(args, wl, world, rank, local):
     cm = list(synth.trap_modulation(wl["seed"], 8, 0.05))
     psi0 = synth.gaussian_state(n, h, wl["widths"], 0.01, 1)
     target = synth.gaussian_state(n, h, (1.1, 0.9, 0.5), 0.01, 2)
-    K = args.steps if args.steps > 20 else 1000
+    K = 1000 if args.steps_default else args.steps  # the adjoint workload's 1000 steps unless --steps
     every = 32
     out = {}
     for fp64 in (False, True):
