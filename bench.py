@@ -221,7 +221,7 @@ def main():
 
     import torch
     from paper_1601_04640_gb300 import build as gbuild
-    from paper_1601_04640_gb300 import dgpe, synth
+    from paper_1601_04640_gb300 import dgpe, shard, synth
     if args.workload == "batched2d":
         return bench_batched(args, wl, world, rank, local)
     if args.workload == "adjoint":
@@ -273,10 +273,7 @@ def main():
         barrier()
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
+        ms_max = shard.max_over_ranks(ms)
         obs = S.observables()
         # per-pass durations (passes launched one by one, events between them)
         passes = dgpe.dgpe_profile_steps(S.h, max(3, args.steps // 2))
@@ -332,10 +329,7 @@ def main():
                 dgpe._check(lib.dgpe_get_psi(S.h, host_out.data_ptr(), sites), S.h)
             barrier()
             te = time.perf_counter() - t0
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            if world > 1:
-                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            f["e2e"] = {"value": world * sites * ke / float(tt.item()), "unit": "site-updates/s",
+            f["e2e"] = {"value": world * sites * ke / shard.max_over_ranks(te), "unit": "site-updates/s",
                         "h2d_bytes_per_step": 16 * sites, "d2h_bytes_per_step": 16 * sites,
                         "steps": ke}
         S.close()
@@ -416,17 +410,23 @@ def _peak_line(metric, value, unit, steps, warmup, ms, dtype, cfg, world, **extr
 
 
 def bench_batched(args, wl, world, rank, local):
-    """512 independent 2D problems stepped by one graph launch per step."""
+    """512 independent 2D problems stepped by one graph launch per step.  With
+    N ranks the sweep is partitioned by cost (shard.partition): each rank steps
+    its share, the only exchange is a host-side gather of the results."""
     import torch
     from paper_1601_04640_gb300 import build as gbuild
-    from paper_1601_04640_gb300 import dgpe, synth
+    from paper_1601_04640_gb300 import dgpe, shard, synth
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     gbuild.build()
     stream = torch.cuda.Stream()
-    probs = synth.batched_problems(4640 + rank, 512)
+    sweep = synth.batched_problems(4640, 512)
+    parts = shard.partition(sweep, world)
+    mine = parts[rank]
+    probs = [sweep[i] for i in mine]
+    sweep_sites = sum(q["n"][0] * q["n"][1] for q in sweep)
     hbm_peak, peak_kind = peaks()
     states = []
     for q in probs:
@@ -452,15 +452,12 @@ def bench_batched(args, wl, world, rank, local):
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = shard.max_over_ranks(ms)
     sites = info["sites"]
     per_step = ms / args.steps
     gbs = info["bytes_per_step"] / (per_step * 1e-3) / 1e9
     sizes = {}
-    for q in probs:
+    for q in sweep:
         sizes[q["n"][0]] = sizes.get(q["n"][0], 0) + 1
     # end to end: every step copies all 512 states in from the host and back
     ke = 2
@@ -471,8 +468,13 @@ def bench_batched(args, wl, world, rank, local):
         B.step(1)
         outs = [B.get_psi(i) for i in range(len(probs))]
     te = time.perf_counter() - t0
+    te = shard.max_over_ranks(te)
+    mus = {}
+    for j, i in enumerate(mine):
+        mus[i] = B.observables(j)["mu"]
     obs0 = B.observables(0)
     B.close()
+    mus = shard.gather(mus)
     if rank != 0:
         return
     cpu = None
@@ -492,17 +494,21 @@ def bench_batched(args, wl, world, rank, local):
         cpu = {"value": done / dtc, "unit": "site-updates/s", "cores": oracle.threads(), "kind": "oracle",
                "sample": "2 steps of each of the first %d problems of the sweep" % (i + 1)}
     line = _peak_line("2D batched split-step site-updates/s and % of HBM roofline",
-                      world * sites * args.steps / (ms * 1e-3), "site-updates/s", args.steps, args.warmup,
+                      sweep_sites * args.steps / (ms * 1e-3), "site-updates/s", args.steps, args.warmup,
                       per_step, "f32 (FP64 reductions/tables)",
-                      {"workload": wl["desc"], "problems": len(probs), "sites": sites, "sizes": sizes,
+                      {"workload": wl["desc"], "problems": len(sweep), "sites": sweep_sites, "sizes": sizes,
                        "classes": info["classes"], "l2": "inputs larger than L2 (%d MB of state)" % (8 * sites >> 20),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-                      world,
+                       "parallelism": ("sweep partitioned by cost over %d GPUs (rank 0: %d problems, %d sites; "
+                                       "imbalance %.3f); results gathered on the host" % (
+                                           world, len(probs), sites, shard.imbalance(sweep, parts)))
+                       if world > 1 else "single GPU",
+                       "results_gathered": len(mus)},
+                      world, scaling="strong" if world > 1 else "weak",
                       roofline={"bound": "hbm", "kernel": "whole batched step", "achieved": gbs,
                                 "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": peak_kind,
                                 "traffic": None, "algorithmic_bytes_per_step": info["bytes_per_step"]},
-                      e2e={"value": sites * ke / te, "unit": "site-updates/s", "h2d_bytes_per_step": 16 * sites,
-                           "d2h_bytes_per_step": 16 * sites},
+                      e2e={"value": sweep_sites * ke / te, "unit": "site-updates/s",
+                           "h2d_bytes_per_step": 16 * sweep_sites, "d2h_bytes_per_step": 16 * sweep_sites},
                       gpu_launches=info["launches_per_step"] * args.steps, clocks=clocks, cpu_baseline=cpu,
                       create_s=t_create, observables_problem0={"mu": obs0["mu"], "norm": obs0["norm"]})
     print(json.dumps(line))
