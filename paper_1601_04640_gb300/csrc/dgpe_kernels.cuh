@@ -170,6 +170,12 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 #define DGPE_W_FFT_F32 16  // FP32 strided transforms: columns per tile
 #endif
 #define DGPE_MINB(R) 2
+// The density/R2C and strided transform passes read their twiddles from a
+// shared copy made once per block (1) or from global memory through L1 (0):
+// the copy relieves the L1TEX pipe, the FP64 transforms' top stall (1-3 %).
+#ifndef DGPE_TW_SMEM
+#define DGPE_TW_SMEM 1
+#endif
 #ifndef DGPE_MINB_FFT_F32
 #define DGPE_MINB_FFT_F32 4
 #endif
@@ -182,6 +188,16 @@ template <typename R> struct Pad { static constexpr int W = 128 / (int)sizeof(cx
 #endif
 #define DGPE_MINB_P1(R) (sizeof(R) == 4 ? DGPE_MINB_P1_F32 : 2)
 #define DGPE_MINB_CN(R) (sizeof(R) == 4 ? DGPE_MINB_CN_F32 : 2)
+
+// Copy the n twiddles of an axis into shared memory (all threads take part;
+// the caller's next barrier publishes them).
+template <typename R>
+__device__ __forceinline__ const cx<R> *stage_twiddles(cx<R> *dst, const cx<R> *__restrict__ tw, int n) {
+  if (!DGPE_TW_SMEM) return tw;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = tw[i];
+  __syncthreads();
+  return dst;
+}
 
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
 template <typename R, int EPT, int SRC, bool POW2>
@@ -207,7 +223,9 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
     return mk<R>(d0, d1);
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
-  tile_fft<R, EPT, false, false, PW, POW2>(zt, SL, 1, A.LP, A.pl, A.tw, load, store);
+  __shared__ __align__(16) cx<R> s_tw[DGPE_TW_SMEM ? 512 : 1];
+  const cx<R> *tw = stage_twiddles<R>(s_tw, A.tw, n);
+  tile_fft<R, EPT, false, false, PW, POW2>(zt, SL, 1, A.LP, A.pl, tw, load, store);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
   const int nh = n / 2 + 1;
@@ -262,6 +280,9 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     const int row = 2 * p0 + t;
     s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
   }
+  // x twiddles: read from global memory here (a shared copy measured slower
+  // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM)
+  const cx<R> *s_twp = A.tw;
   if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
     // every load of the tile is issued before any is used (2 LP n = CL T)
@@ -339,7 +360,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       apply_e(2 * l, a, v.x);
       apply_e(2 * l + 1, a, v.y);
     };
-    tile_fft<R, EPT, true, false, PW, POW2>(zt, A.pitchz, 1, A.LP, A.pl, A.tw, load, store);
+    tile_fft<R, EPT, true, false, PW, POW2>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store);
   } else if (MODE == 0) {
     for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
@@ -387,6 +408,8 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
   __shared__ double red[32];
+  __shared__ __align__(16) cx<R> s_tw[DGPE_TW_SMEM ? 512 : 1];
+  const cx<R> *tw = stage_twiddles<R>(s_tw, A.tw, A.n);
   const int W = A.W;
   const int c0 = blockIdx.x * W;
   const size_t base = (size_t)blockIdx.y * A.ostride + c0;
@@ -399,17 +422,17 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
     if (c0 + l < A.ncols) spec[base + a * es + l] = v;
   };
   if (MODE == 0) {
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, gstore);
   } else if (MODE == 1) {
-    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, gstore);
   } else if (MODE == 2) {
     auto mstore = [&](int l, int a, cx<R> v) {
       const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
       sm[a * W + l] = cscale(v, u);
     };
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, mstore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, mstore);
     auto sload = [&](int l, int a) -> cx<R> { return sm[a * W + l]; };
-    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, sload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, tw, sload, gstore);
   } else {
     double acc = 0.0;
     auto astore = [&](int l, int a, cx<R> v) {
@@ -419,7 +442,7 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
         acc += w * (double)A.U[base + a * es + l] * ((double)v.x * v.x + (double)v.y * v.y);
       }
     };
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, A.tw, gload, astore);
+    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, astore);
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
