@@ -188,6 +188,59 @@ template <int RAD, bool INV, typename C> __device__ __forceinline__ void dft(C *
   else if constexpr (RAD == 16) dft16<INV>(v);
 }
 
+// ------------------------------------ FMA form of a twiddled radix-2^L DFT
+// Y_q = sum_r u_r w^r W_R^{rq} (the inputs of a Stockham stage times their
+// twiddles w^r, then the radix-R DFT) as L layers of radix-2 butterflies:
+// splitting r into even and odd halves gives Y_q = E_q + (w W_R^q) O_q and
+// Y_{q+R/2} = E_q - (w W_R^q) O_q, where E and O are the same problem of size
+// R/2 with twiddle w^2.  Bottom-up with the leaves in bit-reversed order, the
+// size-S combine uses the roots w^{R/S} W_S^q, q < S/2 (n-th root index
+// (R/S) rho + q n/S for w = root rho).  Each root c + i s is tabulated as
+// (t, fx, fy, sw): for |c| >= |s|, t = s/c and (fx, fy) = (c, c); otherwise
+// the root is i (s - i c), t = -c/s, (fx, fy) = (-s, s) and sw = 1.  Then
+// w b = (fx p.x, fy p.y) with v = (b.x - t b.y, b.y + t b.x) and p = v or v
+// swapped, and a butterfly a +- w b is six FMAs (two for v, four for the
+// outputs) with |t| <= 1, instead of a complex product and four additions.
+// This is the rotation-by-ratio device of S. Goedecker's FFT algorithms for
+// machines with fused multiply-add.  The swap is an integer select.
+__device__ __forceinline__ void bfly_fma(double2 &a, double2 &b, const double4 P) {
+  const double vx = fma(-P.x, b.y, b.x), vy = fma(P.x, b.x, b.y);
+  const bool sw = __double_as_longlong(P.w) != 0;
+  const double px = sw ? vy : vx, py = sw ? vx : vy;
+  const double ax = a.x, ay = a.y;
+  a = make_double2(fma(P.y, px, ax), fma(P.z, py, ay));
+  b = make_double2(fma(-P.y, px, ax), fma(-P.z, py, ay));
+}
+template <int R> struct BitRev {
+  static constexpr int of(int r) {
+    int o = 0;
+    for (int m = R >> 1, b = 1; m > 0; m >>= 1, b <<= 1)
+      if (r & b) o |= m;
+    return o;
+  }
+};
+// u: the stage's R inputs in natural order, replaced by Y_0..Y_{R-1};
+// rho: the root index of w; n: line length; T: the tabulated roots (n of them)
+template <int RAD>
+__device__ __forceinline__ void tw_dft_fma(double2 *u, int rho, int n, const double4 *__restrict__ T) {
+  double2 x[RAD];
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) x[BitRev<RAD>::of(r)] = u[r];
+#pragma unroll
+  for (int S = 2; S <= RAD; S <<= 1) {
+    const int half = S / 2, ns = n / S;
+    const int base = (RAD / S) * rho;
+#pragma unroll
+    for (int q = 0; q < half; ++q) {
+      const double4 P = T[(base + q * ns) & (n - 1)];
+#pragma unroll
+      for (int g = 0; g < RAD; g += S) bfly_fma(x[g + q], x[g + q + half], P);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) u[r] = x[r];
+}
+
 // ------------------------------------------------- Stockham FFT over a tile
 // Radix sequence of one line length (forward order; the inverse runs it
 // reversed so that its first stage reads what the forward's last wrote).
@@ -226,10 +279,11 @@ struct StageIdx {
 // outputs are in natural order).  Each thread owns EPT / RAD butterflies, so
 // all of its values stay in registers across the barrier that separates the
 // reads from the writes (in-place update).
-template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, bool POW2, class Load, class Store>
+template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, bool POW2, bool FMA, class Load,
+          class Store>
 __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const StageIdx &I, bool first,
-                                          bool last, const cx<R> *__restrict__ tw, Load &load,
-                                          Store &store) {
+                                          bool last, const cx<R> *__restrict__ tw,
+                                          const double4 *__restrict__ tf, Load &load, Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
   const int T = blockDim.x, t = threadIdx.x;
@@ -260,13 +314,19 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const Stage
     }
     if (!first) {
       const int k = POW2 ? (j & (Ns - 1)) : (j % Ns);
+      if constexpr (FMA && (RAD & (RAD - 1)) == 0) {
+        tw_dft_fma<RAD>(reinterpret_cast<double2 *>(u), k * tstride, I.n, tf);
+      } else {
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        cx<R> w = tw[k * r * tstride];
-        u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
+        for (int r = 1; r < RAD; ++r) {
+          cx<R> w = tw[k * r * tstride];
+          u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
+        }
+        dft<RAD, INV>(u);
       }
+    } else {
+      dft<RAD, INV>(u);
     }
-    dft<RAD, INV>(u);
   }
   __syncthreads();
 #pragma unroll
@@ -289,9 +349,13 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const Stage
 }
 
 // Full transform of every line of the tile.  tw[t] = exp(-2 pi i t / n).
-template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, bool POW2 = true, class Load, class Store>
+// FMA (FP64, power-of-two lengths): the twiddled stages use tw_dft_fma with
+// the tabulated roots tf (exp(-2 pi i t/n) forward, exp(+2 pi i t/n) inverse).
+template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, bool POW2 = true, bool FMA = false,
+          class Load, class Store>
 __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
-                         const cx<R> *__restrict__ tw, Load load, Store store) {
+                         const cx<R> *__restrict__ tw, Load load, Store store,
+                         const double4 *__restrict__ tf = nullptr) {
   StageIdx I;
   I.n = pl.n;
   I.nlines = nlines;
@@ -306,12 +370,12 @@ __device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &p
     I.lr = (rad == 2) ? 1 : (rad == 4) ? 2 : (rad == 8) ? 3 : (rad == 16) ? 4 : 0;
     I.lnbl = I.ln - I.lr;
     switch (rad) {
-      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
-      case 3: if constexpr (EPT % 3 == 0 && !POW2) fft_stage<R, EPT, 3, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
-      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
-      case 5: if constexpr (EPT % 5 == 0 && !POW2) fft_stage<R, EPT, 5, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
-      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
-      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST, PADW, POW2>(sm, SL, SA, I, first, last, tw, load, store); break;
+      case 2: if constexpr (EPT % 2 == 0) fft_stage<R, EPT, 2, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
+      case 3: if constexpr (EPT % 3 == 0 && !POW2) fft_stage<R, EPT, 3, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
+      case 4: if constexpr (EPT % 4 == 0) fft_stage<R, EPT, 4, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
+      case 5: if constexpr (EPT % 5 == 0 && !POW2) fft_stage<R, EPT, 5, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
+      case 8: if constexpr (EPT % 8 == 0) fft_stage<R, EPT, 8, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
+      case 16: if constexpr (EPT % 16 == 0) fft_stage<R, EPT, 16, INV, LINE_FAST, PADW, POW2, FMA>(sm, SL, SA, I, first, last, tw, tf, load, store); break;
       default: break;
     }
     I.Ns *= rad;

@@ -173,6 +173,8 @@ template <typename R> struct EngineT : Engine {
   Cx *psi = nullptr, *spec = nullptr;
   R *U = nullptr, *phi_tmp = nullptr;
   Cx *tw[3] = {nullptr, nullptr, nullptr};
+  // FMA-form roots per axis (FP64; forward and inverse): (t, fx, fy, swap)
+  double4 *twf[3] = {nullptr, nullptr, nullptr}, *twi[3] = {nullptr, nullptr, nullptr};
   R *vt[3] = {nullptr, nullptr, nullptr};
   void *cntab[3] = {nullptr, nullptr, nullptr};
   double *prm = nullptr, *partial = nullptr, *obs_part = nullptr, *dip_part = nullptr, *obs_out = nullptr;
@@ -229,7 +231,8 @@ template <typename R> struct EngineT : Engine {
     void *bufs[] = {psi, spec, U, phi_tmp, tw[0], tw[1], tw[2], vt[0], vt[1], vt[2],
                     cntab[0], cntab[1], cntab[2], prm, partial, obs_part, dip_part, obs_out,
                     dstep, counter, stage, adjG, adjT, adj_phi, adj_sig, adj_ksig, adj_part,
-                    adj_acc, cntab_adj[0], cntab_adj[1], cntab_adj[2]};
+                    adj_acc, cntab_adj[0], cntab_adj[1], cntab_adj[2], twf[0], twf[1], twf[2],
+                    twi[0], twi[1], twi[2]};
     for (void *b : bufs)
       if (b) cudaFree(b);
     for (Cx *b : ckpts) cudaFree(b);
@@ -311,6 +314,22 @@ template <typename R> struct EngineT : Engine {
       }
       if ((rc = dalloc(&tw[a], ns[a]))) return rc;
       if ((rc = upload(tw[a], w))) return rc;
+      if (sizeof(R) == 8) {
+        // root c + i s of exp(-+2 pi i t/n): |c| >= |s| -> (s/c, c, c, 0);
+        // else the root is i (s - i c) -> (-c/s, -s, s, 1)
+        for (int dir = 0; dir < 2; ++dir) {
+          std::vector<double4> f(ns[a]);
+          for (int t = 0; t < ns[a]; ++t) {
+            const double ang = (dir ? 2.0 : -2.0) * M_PI * (double)t / (double)ns[a];
+            const double c = std::cos(ang), sn = std::sin(ang);
+            if (std::fabs(c) >= std::fabs(sn)) f[t] = make_double4(sn / c, c, c, 0.0);
+            else f[t] = make_double4(-c / sn, -sn, sn, 1.0);
+          }
+          double4 **dst = dir ? &twi[a] : &twf[a];
+          if ((rc = dalloc(dst, ns[a]))) return rc;
+          if ((rc = upload(*dst, f))) return rc;
+        }
+      }
     }
     for (int a = 0; a < 3; ++a) {
       const int n = (a < dim) ? ns[a] : 1;
@@ -549,14 +568,15 @@ template <typename R> struct EngineT : Engine {
     int rc = with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
+      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
       int r;
-      if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2>, x4_smem))) return r;
-      if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2>, x4_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2>, x_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2, FM>, x4_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2, FM>, x4_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM>, x_smem))) return r;
       return DGPE_OK;
     });
     if (rc) return rc;
@@ -565,11 +585,12 @@ template <typename R> struct EngineT : Engine {
       rc = with_svar<EPT_S>(var[a], [&](auto EPc, auto P2c) -> int {
         constexpr int EP = decltype(EPc)::value;
         constexpr bool P2 = decltype(P2c)::value;
+      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
         int r;
-        if ((r = smem_attr(k_fft_strided<R, EP, 0, P2>, fs))) return r;
-        if ((r = smem_attr(k_fft_strided<R, EP, 1, P2>, fs))) return r;
-        if ((r = smem_attr(k_fft_strided<R, EP, 2, P2>, fs))) return r;
-        if ((r = smem_attr(k_fft_strided<R, EP, 3, P2>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 0, P2, FM>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 1, P2, FM>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 2, P2, FM>, fs))) return r;
+        if ((r = smem_attr(k_fft_strided<R, EP, 3, P2, FM>, fs))) return r;
         return DGPE_OK;
       });
       if (rc) return rc;
@@ -600,7 +621,7 @@ template <typename R> struct EngineT : Engine {
   XArgs<R> xargs() const {
     XArgs<R> A{};
     A.psi = psi; A.spec = spec; A.phi_out = phi_tmp; A.prm = prm; A.step = dstep;
-    A.tw = tw[0]; A.vx = vt[0]; A.vy = vt[1]; A.vz = vt[2]; A.cntab = cntab[0];
+    A.tw = tw[0]; A.twf = twf[0]; A.twi = twi[0]; A.vx = vt[0]; A.vy = vt[1]; A.vz = vt[2]; A.cntab = cntab[0];
     A.pl = plx; A.nx = nx; A.ny = ny; A.nrows = nrows; A.px = px; A.LP = x_LP;
     A.pitchz = x_pitchz; A.pitch = x_pitch; A.TPL = x_TPL; A.C = x_C;
     A.imag = imag; A.has_dip = has_dip ? 1 : 0; A.tau = tau[0];
@@ -609,6 +630,7 @@ template <typename R> struct EngineT : Engine {
   SArgs<R> sargs(const FtCfg &f) const {
     SArgs<R> A{};
     A.spec = spec; A.U = U; A.partial = dip_part; A.tw = tw[f.axis]; A.pl = f.pl;
+    A.twf = twf[f.axis]; A.twi = twi[f.axis];
     A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = f.W; A.nxh = nx / 2;
     return A;
   }
@@ -617,11 +639,12 @@ template <typename R> struct EngineT : Engine {
     with_svar<EPT_S>(var[f.axis], [&](auto EPc, auto P2c) -> int {
       constexpr int EP = decltype(EPc)::value;
       constexpr bool P2 = decltype(P2c)::value;
+      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
       switch (mode) {
-        case 0: k_fft_strided<R, EP, 0, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
-        case 1: k_fft_strided<R, EP, 1, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
-        case 2: k_fft_strided<R, EP, 2, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
-        default: k_fft_strided<R, EP, 3, P2><<<f.grid, f.T, f.smem, s>>>(A); break;
+        case 0: k_fft_strided<R, EP, 0, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
+        case 1: k_fft_strided<R, EP, 1, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
+        case 2: k_fft_strided<R, EP, 2, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
+        default: k_fft_strided<R, EP, 3, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
       }
       return DGPE_OK;
     });
@@ -672,8 +695,9 @@ template <typename R> struct EngineT : Engine {
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      if (dens_in) k_dens_r2c_x<R, EX, 1, P2><<<x_grid, x_T, x4_smem, s>>>(A);
-      else k_dens_r2c_x<R, EX, 0, P2><<<x_grid, x_T, x4_smem, s>>>(A);
+      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      if (dens_in) k_dens_r2c_x<R, EX, 1, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
+      else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
     launched(1);
@@ -694,15 +718,16 @@ template <typename R> struct EngineT : Engine {
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
+      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
       if (mode == 0) {
-        if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
-        else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2><<<x_grid, x_T, x_smem, s>>>(A);
+        if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
+        else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 3) {
-        k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 1) {
-        k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
       } else {
-        k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
       }
       return DGPE_OK;
     });

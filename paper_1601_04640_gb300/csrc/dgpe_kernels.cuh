@@ -42,6 +42,7 @@ template <typename R> struct XArgs {  // x-line passes
   const double *prm;
   const long long *step;
   const cx<R> *tw;
+  const double4 *twf, *twi;  // FMA-form roots of the axis (FP64 power-of-two; forward, inverse)
   const R *vx, *vy, *vz;
   const void *cntab;
   FftPlan pl;
@@ -56,6 +57,7 @@ template <typename R> struct SArgs {  // strided FFT passes over the spectrum
   const R *U;
   double *partial;
   const cx<R> *tw;
+  const double4 *twf, *twi;  // FMA-form roots of the axis (FP64 power-of-two; forward, inverse)
   FftPlan pl;
   long long estride, ostride;
   int n, ncols, W, nxh;
@@ -208,8 +210,17 @@ __device__ __forceinline__ const cx<R> *stage_twiddles(cx<R> *dst, const cx<R> *
   return dst;
 }
 
+// Copy the n FMA-form roots of an axis into shared memory (all threads; the
+// barrier publishes them).  At most 512 roots.
+__device__ __forceinline__ const double4 *stage_roots(double4 *dst, const double4 *__restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return dst;
+}
+
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
-template <typename R, int EPT, int SRC, bool POW2>
+// FMA: twiddled stages in FMA form (tile_fft), roots from A.twf.
+template <typename R, int EPT, int SRC, bool POW2, bool FMA = false>
 __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
@@ -232,9 +243,11 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
     return mk<R>(d0, d1);
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
-  __shared__ __align__(16) cx<R> s_tw[DGPE_TW_SMEM ? 512 : 1];
-  const cx<R> *tw = stage_twiddles<R>(s_tw, A.tw, n);
-  tile_fft<R, EPT, false, false, PW, POW2>(zt, SL, 1, A.LP, A.pl, tw, load, store);
+  __shared__ __align__(16) cx<R> s_tw[(DGPE_TW_SMEM && !FMA) ? 512 : 1];
+  __shared__ __align__(16) double4 s_rt[FMA ? 512 : 1];
+  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, n);
+  const double4 *rt = FMA ? stage_roots(s_rt, A.twf, n) : nullptr;
+  tile_fft<R, EPT, false, false, PW, POW2, FMA>(zt, SL, 1, A.LP, A.pl, tw, load, store, rt);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
   const int nh = n / 2 + 1;
@@ -249,9 +262,9 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
     if (r1 < nrows) A.spec[(size_t)r1 * A.px + k] = X1;
   }
 }
-template <typename R, int EPT, int SRC = 0, bool POW2 = true>
+template <typename R, int EPT, int SRC = 0, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x(XArgs<R> A) {
-  dens_r2c_x_body<R, EPT, SRC, POW2>(A);
+  dens_r2c_x_body<R, EPT, SRC, POW2, FMA>(A);
 }
 // batched: one problem per blockIdx.z
 template <typename R, int EPT, bool POW2>
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
 // MODE 2: CN_x alone (the reverse step applies it to the adjoint field).
 // MODE 3: C2R_x and the exponential, no CN (a separate CN_x pass follows).
-template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2>
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false>
 __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
@@ -290,8 +303,12 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
   }
   // x twiddles: read from global memory here (a shared copy measured slower
-  // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM)
+  // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM);
+  // the FMA-form roots (FP64) from a shared copy
   const cx<R> *s_twp = A.tw;
+  __shared__ __align__(16) double4 s_rt[(FMA && MODE != 2) ? 512 : 1];
+  const double4 *rt = nullptr;
+  if constexpr (FMA && MODE != 2) rt = stage_roots(s_rt, A.twi, n);
   if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
     // every load of the tile is issued before any is used (2 LP n = CL T)
@@ -369,7 +386,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       apply_e(2 * l, a, v.x);
       apply_e(2 * l + 1, a, v.y);
     };
-    tile_fft<R, EPT, true, false, PW, POW2>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store);
+    tile_fft<R, EPT, true, false, PW, POW2, FMA>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store, rt);
   } else if (MODE == 0) {
     for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
@@ -399,9 +416,9 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
   }
 }
-template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true>
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx(XArgs<R> A) {
-  c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2>(A);
+  c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2, FMA>(A);
 }
 template <typename R, typename Coef, int EPT, int CL, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
@@ -412,13 +429,20 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_ba
 // ------------------------------------------------- P5 / P6 / P7 (strided)
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
-template <typename R, int EPT, int MODE, bool POW2>
+template <typename R, int EPT, int MODE, bool POW2, bool FMA = false>
 __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
   __shared__ double red[32];
-  __shared__ __align__(16) cx<R> s_tw[DGPE_TW_SMEM ? 512 : 1];
-  const cx<R> *tw = stage_twiddles<R>(s_tw, A.tw, A.n);
+  __shared__ __align__(16) cx<R> s_tw[(DGPE_TW_SMEM && !FMA) ? 512 : 1];
+  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, A.n);
+  // FMA-form roots: forward (modes 0, 2, 3) and inverse (modes 1, 2)
+  constexpr bool NF = FMA && MODE != 1, NI = FMA && (MODE == 1 || MODE == 2);
+  __shared__ __align__(16) double4 s_rf[NF ? 512 : 1];
+  __shared__ __align__(16) double4 s_ri[NI ? 512 : 1];
+  const double4 *rf = nullptr, *ri = nullptr;
+  if constexpr (NF) rf = stage_roots(s_rf, A.twf, A.n);
+  if constexpr (NI) ri = stage_roots(s_ri, A.twi, A.n);
   const int W = A.W;
   const int c0 = blockIdx.x * W;
   const size_t base = (size_t)blockIdx.y * A.ostride + c0;
@@ -431,17 +455,17 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
     if (c0 + l < A.ncols) spec[base + a * es + l] = v;
   };
   if (MODE == 0) {
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, gstore);
+    tile_fft<R, EPT, false, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, gstore, rf);
   } else if (MODE == 1) {
-    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, gstore, ri);
   } else if (MODE == 2) {
     auto mstore = [&](int l, int a, cx<R> v) {
       const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
       sm[a * W + l] = cscale(v, u);
     };
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, mstore);
+    tile_fft<R, EPT, false, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, mstore, rf);
     auto sload = [&](int l, int a) -> cx<R> { return sm[a * W + l]; };
-    tile_fft<R, EPT, true, true, 0, POW2>(sm, 1, W, W, A.pl, tw, sload, gstore);
+    tile_fft<R, EPT, true, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, sload, gstore, ri);
   } else {
     double acc = 0.0;
     auto astore = [&](int l, int a, cx<R> v) {
@@ -451,14 +475,14 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
         acc += w * (double)A.U[base + a * es + l] * ((double)v.x * v.x + (double)v.y * v.y);
       }
     };
-    tile_fft<R, EPT, false, true, 0, POW2>(sm, 1, W, W, A.pl, tw, gload, astore);
+    tile_fft<R, EPT, false, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, astore, rf);
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
-template <typename R, int EPT, int MODE, bool POW2 = true>
+template <typename R, int EPT, int MODE, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided(SArgs<R> A) {
-  fft_strided_body<R, EPT, MODE, POW2>(A);
+  fft_strided_body<R, EPT, MODE, POW2, FMA>(A);
 }
 template <typename R, int EPT, int MODE, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
