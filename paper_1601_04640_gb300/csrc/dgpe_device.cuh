@@ -19,6 +19,10 @@ template <typename R> struct V2;
 template <> struct V2<double> { using T = double2; };
 template <> struct V2<float> { using T = float2; };
 template <typename R> using cx = typename V2<R>::T;
+template <typename R> struct V4;
+template <> struct V4<double> { using T = double4; };
+template <> struct V4<float> { using T = float4; };
+template <typename R> using rt4 = typename V4<R>::T;  // an FMA-form root (t, fx, fy, swap)
 
 template <typename R> __device__ __forceinline__ cx<R> mk(R x, R y) {
   cx<R> c; c.x = x; c.y = y; return c;
@@ -211,6 +215,14 @@ __device__ __forceinline__ void bfly_fma(double2 &a, double2 &b, const double4 P
   a = make_double2(fma(P.y, px, ax), fma(P.z, py, ay));
   b = make_double2(fma(-P.y, px, ax), fma(-P.z, py, ay));
 }
+__device__ __forceinline__ void bfly_fma(float2 &a, float2 &b, const float4 P) {
+  const float vx = fmaf(-P.x, b.y, b.x), vy = fmaf(P.x, b.x, b.y);
+  const bool sw = __float_as_int(P.w) != 0;
+  const float px = sw ? vy : vx, py = sw ? vx : vy;
+  const float ax = a.x, ay = a.y;
+  a = make_float2(fmaf(P.y, px, ax), fmaf(P.z, py, ay));
+  b = make_float2(fmaf(-P.y, px, ax), fmaf(-P.z, py, ay));
+}
 template <int R> struct BitRev {
   static constexpr int of(int r) {
     int o = 0;
@@ -221,9 +233,9 @@ template <int R> struct BitRev {
 };
 // u: the stage's R inputs in natural order, replaced by Y_0..Y_{R-1};
 // rho: the root index of w; n: line length; T: the tabulated roots (n of them)
-template <int RAD>
-__device__ __forceinline__ void tw_dft_fma(double2 *u, int rho, int n, const double4 *__restrict__ T) {
-  double2 x[RAD];
+template <int RAD, typename R>
+__device__ __forceinline__ void tw_dft_fma(cx<R> *u, int rho, int n, const rt4<R> *__restrict__ T) {
+  cx<R> x[RAD];
 #pragma unroll
   for (int r = 0; r < RAD; ++r) x[BitRev<RAD>::of(r)] = u[r];
 #pragma unroll
@@ -232,7 +244,7 @@ __device__ __forceinline__ void tw_dft_fma(double2 *u, int rho, int n, const dou
     const int base = (RAD / S) * rho;
 #pragma unroll
     for (int q = 0; q < half; ++q) {
-      const double4 P = T[(base + q * ns) & (n - 1)];
+      const rt4<R> P = T[(base + q * ns) & (n - 1)];
 #pragma unroll
       for (int g = 0; g < RAD; g += S) bfly_fma(x[g + q], x[g + q + half], P);
     }
@@ -283,7 +295,7 @@ template <typename R, int EPT, int RAD, bool INV, bool LINE_FAST, int PADW, bool
           class Store>
 __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const StageIdx &I, bool first,
                                           bool last, const cx<R> *__restrict__ tw,
-                                          const double4 *__restrict__ tf, Load &load, Store &store) {
+                                          const rt4<R> *__restrict__ tf, Load &load, Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
   const int T = blockDim.x, t = threadIdx.x;
@@ -315,7 +327,7 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const Stage
     if (!first) {
       const int k = POW2 ? (j & (Ns - 1)) : (j % Ns);
       if constexpr (FMA && (RAD & (RAD - 1)) == 0) {
-        tw_dft_fma<RAD>(reinterpret_cast<double2 *>(u), k * tstride, I.n, tf);
+        tw_dft_fma<RAD, R>(u, k * tstride, I.n, tf);
       } else {
 #pragma unroll
         for (int r = 1; r < RAD; ++r) {
@@ -349,13 +361,13 @@ __device__ __forceinline__ void fft_stage(cx<R> *sm, int SL, int SA, const Stage
 }
 
 // Full transform of every line of the tile.  tw[t] = exp(-2 pi i t / n).
-// FMA (FP64, power-of-two lengths): the twiddled stages use tw_dft_fma with
+// FMA (power-of-two lengths): the twiddled stages use tw_dft_fma with
 // the tabulated roots tf (exp(-2 pi i t/n) forward, exp(+2 pi i t/n) inverse).
 template <typename R, int EPT, bool INV, bool LINE_FAST, int PADW, bool POW2 = true, bool FMA = false,
           class Load, class Store>
-__device__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
+__device__ __forceinline__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, const FftPlan &pl,
                          const cx<R> *__restrict__ tw, Load load, Store store,
-                         const double4 *__restrict__ tf = nullptr) {
+                         const rt4<R> *__restrict__ tf = nullptr) {
   StageIdx I;
   I.n = pl.n;
   I.nlines = nlines;

@@ -157,6 +157,9 @@ inline double wavenumber(int j, int n, double h) {
     }                                                                        \
   } while (0)
 
+#ifndef DGPE_FFT_FMA_F32
+#define DGPE_FFT_FMA_F32 0  // FP32 density and strided transforms in FMA form too (measured 3 % slower)
+#endif
 template <typename R> struct EngineT : Engine {
   typedef cx<R> Cx;
   static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFTs, power-of-two lengths
@@ -173,8 +176,8 @@ template <typename R> struct EngineT : Engine {
   Cx *psi = nullptr, *spec = nullptr;
   R *U = nullptr, *phi_tmp = nullptr;
   Cx *tw[3] = {nullptr, nullptr, nullptr};
-  // FMA-form roots per axis (FP64; forward and inverse): (t, fx, fy, swap)
-  double4 *twf[3] = {nullptr, nullptr, nullptr}, *twi[3] = {nullptr, nullptr, nullptr};
+  // FMA-form roots per axis (forward and inverse): (t, fx, fy, swap), built in FP64
+  rt4<R> *twf[3] = {nullptr, nullptr, nullptr}, *twi[3] = {nullptr, nullptr, nullptr};
   R *vt[3] = {nullptr, nullptr, nullptr};
   void *cntab[3] = {nullptr, nullptr, nullptr};
   double *prm = nullptr, *partial = nullptr, *obs_part = nullptr, *dip_part = nullptr, *obs_out = nullptr;
@@ -314,18 +317,21 @@ template <typename R> struct EngineT : Engine {
       }
       if ((rc = dalloc(&tw[a], ns[a]))) return rc;
       if ((rc = upload(tw[a], w))) return rc;
-      if (sizeof(R) == 8) {
+      {
         // root c + i s of exp(-+2 pi i t/n): |c| >= |s| -> (s/c, c, c, 0);
         // else the root is i (s - i c) -> (-c/s, -s, s, 1)
         for (int dir = 0; dir < 2; ++dir) {
-          std::vector<double4> f(ns[a]);
+          std::vector<rt4<R>> f(ns[a]);
           for (int t = 0; t < ns[a]; ++t) {
             const double ang = (dir ? 2.0 : -2.0) * M_PI * (double)t / (double)ns[a];
             const double c = std::cos(ang), sn = std::sin(ang);
-            if (std::fabs(c) >= std::fabs(sn)) f[t] = make_double4(sn / c, c, c, 0.0);
-            else f[t] = make_double4(-c / sn, -sn, sn, 1.0);
+            const bool sw = !(std::fabs(c) >= std::fabs(sn));
+            f[t].x = (R)(sw ? -c / sn : sn / c);
+            f[t].y = (R)(sw ? -sn : c);
+            f[t].z = (R)(sw ? sn : c);
+            f[t].w = (R)(sw ? 1.0 : 0.0);
           }
-          double4 **dst = dir ? &twi[a] : &twf[a];
+          rt4<R> **dst = dir ? &twi[a] : &twf[a];
           if ((rc = dalloc(dst, ns[a]))) return rc;
           if ((rc = upload(*dst, f))) return rc;
         }
@@ -568,15 +574,16 @@ template <typename R> struct EngineT : Engine {
     int rc = with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
+      constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       int r;
       if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2, FM>, x4_smem))) return r;
       if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2, FM>, x4_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM>, x_smem))) return r;
-      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM1>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM1>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM1>, x_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM1>, x_smem))) return r;
       return DGPE_OK;
     });
     if (rc) return rc;
@@ -585,7 +592,8 @@ template <typename R> struct EngineT : Engine {
       rc = with_svar<EPT_S>(var[a], [&](auto EPc, auto P2c) -> int {
         constexpr int EP = decltype(EPc)::value;
         constexpr bool P2 = decltype(P2c)::value;
-      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
+      constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
         int r;
         if ((r = smem_attr(k_fft_strided<R, EP, 0, P2, FM>, fs))) return r;
         if ((r = smem_attr(k_fft_strided<R, EP, 1, P2, FM>, fs))) return r;
@@ -639,7 +647,8 @@ template <typename R> struct EngineT : Engine {
     with_svar<EPT_S>(var[f.axis], [&](auto EPc, auto P2c) -> int {
       constexpr int EP = decltype(EPc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
+      constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       switch (mode) {
         case 0: k_fft_strided<R, EP, 0, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
         case 1: k_fft_strided<R, EP, 1, P2, FM><<<f.grid, f.T, f.smem, s>>>(A); break;
@@ -695,7 +704,8 @@ template <typename R> struct EngineT : Engine {
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
+      constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       if (dens_in) k_dens_r2c_x<R, EX, 1, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
@@ -718,16 +728,17 @@ template <typename R> struct EngineT : Engine {
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;
       constexpr bool P2 = decltype(P2c)::value;
-      constexpr bool FM = (sizeof(R) == 8) && P2;  // FMA-form twiddled stages
+      constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
+      constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       if (mode == 0) {
-        if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
-        else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
+        if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
+        else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 3) {
-        k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 1) {
-        k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       } else {
-        k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM><<<x_grid, x_T, x_smem, s>>>(A);
+        k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       }
       return DGPE_OK;
     });

@@ -42,7 +42,7 @@ template <typename R> struct XArgs {  // x-line passes
   const double *prm;
   const long long *step;
   const cx<R> *tw;
-  const double4 *twf, *twi;  // FMA-form roots of the axis (FP64 power-of-two; forward, inverse)
+  const rt4<R> *twf, *twi;  // FMA-form roots of the axis (power-of-two lengths; forward, inverse)
   const R *vx, *vy, *vz;
   const void *cntab;
   FftPlan pl;
@@ -57,7 +57,7 @@ template <typename R> struct SArgs {  // strided FFT passes over the spectrum
   const R *U;
   double *partial;
   const cx<R> *tw;
-  const double4 *twf, *twi;  // FMA-form roots of the axis (FP64 power-of-two; forward, inverse)
+  const rt4<R> *twf, *twi;  // FMA-form roots of the axis (power-of-two lengths; forward, inverse)
   FftPlan pl;
   long long estride, ostride;
   int n, ncols, W, nxh;
@@ -212,8 +212,17 @@ __device__ __forceinline__ const cx<R> *stage_twiddles(cx<R> *dst, const cx<R> *
 
 // Copy the n FMA-form roots of an axis into shared memory (all threads; the
 // barrier publishes them).  At most 512 roots.
-__device__ __forceinline__ const double4 *stage_roots(double4 *dst, const double4 *__restrict__ src, int n) {
+template <typename T> __device__ __forceinline__ const T *stage_roots(T *dst, const T *__restrict__ src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return dst;
+}
+
+// Batched kernels: the block's problem arguments, copied once into shared
+// memory (a by-value copy of a struct whose members are passed on by
+// reference lands in local memory, one local load per field access).
+template <typename T> __device__ __forceinline__ const T &block_args(const T *__restrict__ args, T &dst) {
+  if (threadIdx.x == 0) dst = args[blockIdx.z];
   __syncthreads();
   return dst;
 }
@@ -244,9 +253,9 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
   __shared__ __align__(16) cx<R> s_tw[(DGPE_TW_SMEM && !FMA) ? 512 : 1];
-  __shared__ __align__(16) double4 s_rt[FMA ? 512 : 1];
+  __shared__ __align__(16) rt4<R> s_rt[FMA ? 512 : 1];
   const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, n);
-  const double4 *rt = FMA ? stage_roots(s_rt, A.twf, n) : nullptr;
+  const rt4<R> *rt = FMA ? stage_roots(s_rt, A.twf, n) : nullptr;
   tile_fft<R, EPT, false, false, PW, POW2, FMA>(zt, SL, 1, A.LP, A.pl, tw, load, store, rt);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
@@ -263,13 +272,14 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
   }
 }
 template <typename R, int EPT, int SRC = 0, bool POW2 = true, bool FMA = false>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x(const __grid_constant__ XArgs<R> A) {
   dens_r2c_x_body<R, EPT, SRC, POW2, FMA>(A);
 }
 // batched: one problem per blockIdx.z
 template <typename R, int EPT, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch(const XArgs<R> *__restrict__ args) {
-  const XArgs<R> A = args[blockIdx.z];
+  __shared__ XArgs<R> sA;
+  const XArgs<R> &A = block_args(args, sA);
   if (blockIdx.x * A.LP * 2 >= (unsigned)A.nrows) return;
   dens_r2c_x_body<R, EPT, 0, POW2>(A);
 }
@@ -306,8 +316,8 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM);
   // the FMA-form roots (FP64) from a shared copy
   const cx<R> *s_twp = A.tw;
-  __shared__ __align__(16) double4 s_rt[(FMA && MODE != 2) ? 512 : 1];
-  const double4 *rt = nullptr;
+  __shared__ __align__(16) rt4<R> s_rt[(FMA && MODE != 2) ? 512 : 1];
+  const rt4<R> *rt = nullptr;
   if constexpr (FMA && MODE != 2) rt = stage_roots(s_rt, A.twi, n);
   if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
@@ -417,12 +427,13 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   }
 }
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true, bool FMA = false>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx(XArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx(const __grid_constant__ XArgs<R> A) {
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2, FMA>(A);
 }
 template <typename R, typename Coef, int EPT, int CL, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
-  const XArgs<R> A = args[blockIdx.z];
+  __shared__ XArgs<R> sA;
+  const XArgs<R> &A = block_args(args, sA);
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
 }
 
@@ -438,9 +449,9 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, A.n);
   // FMA-form roots: forward (modes 0, 2, 3) and inverse (modes 1, 2)
   constexpr bool NF = FMA && MODE != 1, NI = FMA && (MODE == 1 || MODE == 2);
-  __shared__ __align__(16) double4 s_rf[NF ? 512 : 1];
-  __shared__ __align__(16) double4 s_ri[NI ? 512 : 1];
-  const double4 *rf = nullptr, *ri = nullptr;
+  __shared__ __align__(16) rt4<R> s_rf[NF ? 512 : 1];
+  __shared__ __align__(16) rt4<R> s_ri[NI ? 512 : 1];
+  const rt4<R> *rf = nullptr, *ri = nullptr;
   if constexpr (NF) rf = stage_roots(s_rf, A.twf, A.n);
   if constexpr (NI) ri = stage_roots(s_ri, A.twi, A.n);
   const int W = A.W;
@@ -481,12 +492,13 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
   }
 }
 template <typename R, int EPT, int MODE, bool POW2 = true, bool FMA = false>
-__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided(SArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided(const __grid_constant__ SArgs<R> A) {
   fft_strided_body<R, EPT, MODE, POW2, FMA>(A);
 }
 template <typename R, int EPT, int MODE, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
-  const SArgs<R> A = args[blockIdx.z];
+  __shared__ SArgs<R> sA;
+  const SArgs<R> &A = block_args(args, sA);
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
 
@@ -573,12 +585,13 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   }
 }
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided(CArgs<R> A) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided(const __grid_constant__ CArgs<R> A) {
   cn_strided_body<R, Coef, CL>(A);
 }
 template <typename R, typename Coef, int CL>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
-  const CArgs<R> A = args[blockIdx.z];
+  __shared__ CArgs<R> sA;
+  const CArgs<R> &A = block_args(args, sA);
   cn_strided_body<R, Coef, CL>(A);
 }
 
@@ -587,7 +600,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(co
 // the other shared buffer are in flight while the current tile is solved.
 // Tile id -> (column block id % nx_blocks, outer index id / nx_blocks).
 template <typename R, typename Coef, int CL>
-__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(CArgs<R> A, int ncb, int ntiles) {
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(const __grid_constant__ CArgs<R> A, int ncb, int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   __shared__ int am_last;
