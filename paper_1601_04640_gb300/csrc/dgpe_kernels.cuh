@@ -760,7 +760,7 @@ template <typename R> struct KtMul<R, cx<R>> {
 // NORM: accumulate the FP64 norm (the final pass of an imaginary-time step);
 // a template flag so that the real-time passes carry no norm arithmetic.
 template <typename R, typename Coef, bool NORM>
-__global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
+__global__ void __launch_bounds__(128) k_cn_lines(const __grid_constant__ LArgs A) {
   __shared__ double red[32];
   __shared__ int am_last;
   typedef cx<R> Cx;
@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(128) k_cn_lines(LArgs A) {
 enum { OBS_N, OBS_X2, OBS_Y2, OBS_Z2, OBS_V, OBS_N2, OBS_KX, OBS_KY, OBS_KZ, OBS_BAD, OBS_COUNT };
 
 template <typename R>
-__global__ void k_obs_sites(OArgs<R> A) {
+__global__ void k_obs_sites(const __grid_constant__ OArgs<R> A) {
   __shared__ double red[32];
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const size_t N = (size_t)nx * ny * nz;
@@ -991,7 +991,7 @@ template <typename R> __device__ __forceinline__ R adj_theta(const AArgs<R> &A, 
 }
 
 template <typename R>
-__global__ void k_adj_sigma(AArgs<R> A) {
+__global__ void k_adj_sigma(const __grid_constant__ AArgs<R> A) {
   __shared__ double red[32];
   double sn = 0.0, sv = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.n; i += (size_t)gridDim.x * blockDim.x) {
@@ -1014,7 +1014,7 @@ __global__ void k_adj_sigma(AArgs<R> A) {
 }
 
 template <typename R>
-__global__ void k_adj_update(AArgs<R> A) {
+__global__ void k_adj_update(const __grid_constant__ AArgs<R> A) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.n; i += (size_t)gridDim.x * blockDim.x) {
     const cx<R> v = A.psi_in[i];
     R dens, v0;
