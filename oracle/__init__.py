@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-KERNELS = {"none": 0, "dipolar3d": 1, "quasi2d": 2}
+KERNELS = {"none": 0, "dipolar3d": 1, "quasi2d": 2, "quasi2d_xz": 3}
 MAXM = 16
 
 
@@ -97,6 +97,9 @@ def load():
         lib.or_kernel_q2d.argtypes = [dp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double]
         lib.or_q2d_value.argtypes = [C.c_double, C.c_double]
         lib.or_q2d_value.restype = C.c_double
+        lib.or_kernel_q2dxz.argtypes = [dp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double]
+        lib.or_q2dxz_value.argtypes = [C.c_double, C.c_double, C.c_double]
+        lib.or_q2dxz_value.restype = C.c_double
         lib.or_dipolar_potential.argtypes = [P, dp, dp]
         lib.or_trap.argtypes = [P, dp]
         lib.or_trap_scale.argtypes = [P, C.c_double]
@@ -165,6 +168,19 @@ def kernel_q2d(n, h, d):
 
 def q2d_value(k, d):
     return load().or_q2d_value(float(k), float(d))
+
+
+def kernel_q2dxz(n, h, d):
+    """Quasi-2D XZ kernel on the (nz, nx) grid: n = (nx, nz), h = (hx, hz)."""
+    U = np.empty((n[1], n[0]), dtype=np.float64)
+    nn = list(n) + [1] * (3 - len(n))
+    hh = list(h) + [1.0] * (3 - len(h))
+    load().or_kernel_q2dxz(U, (C.c_int * 3)(*nn), (C.c_double * 3)(*hh), float(d))
+    return U
+
+
+def q2dxz_value(kx, kz, d):
+    return load().or_q2dxz_value(float(kx), float(kz), float(d))
 
 
 def dipolar_potential(p: Params, dens):

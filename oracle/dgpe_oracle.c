@@ -247,6 +247,31 @@ void or_kernel_q2d(double *U, const int n[3], const double h[3], double d) {
     }
 }
 
+/* Quasi-2D XZ kernel: the grid is the (x, z) plane, the dipoles point along
+ * z (in the plane) and the density has the transverse profile
+ * |phi(y)|^2 = exp(-y^2/d^2) / (sqrt(pi) d).  Averaging the 3D kernel over y
+ * (the profile's pair weight exp(-ky^2 d^2 / 2) in k_y, as for the XY kernel),
+ *   U(kx, kz) = int dky/(2 pi) (4 pi/3) (3 kz^2/(kx^2 + ky^2 + kz^2) - 1) exp(-ky^2 d^2/2),
+ * and with int dky exp(-a ky^2)/(k^2 + ky^2) = (pi/k) erfcx(sqrt(a) k):
+ *   U(kx, kz) = (4 pi/3)/(sqrt(2 pi) d) [3 sqrt(pi/2) (kz^2 d / krho) erfcx(krho d/sqrt 2) - 1],
+ * krho^2 = kx^2 + kz^2.  Limits: U -> (4 pi/3)(3 kz^2/krho^2 - 1) for
+ * krho d >> 1 (in-plane dipoles), U(kx, 0) = U(0) = -(4 pi/3)/(sqrt(2 pi) d). */
+double or_q2dxz_value(double kx, double kz, double d) {
+  double pref = (4.0 * M_PI / 3.0) / (sqrt(2.0 * M_PI) * d);
+  double krho = sqrt(kx * kx + kz * kz);
+  if (krho == 0.0) return -pref;
+  double q = krho * d;
+  return pref * (3.0 * sqrt(M_PI / 2.0) * (kz * kz * d / krho) * erfcx_pos(q / sqrt(2.0)) - 1.0);
+}
+
+void or_kernel_q2dxz(double *U, const int n[3], const double h[3], double d) {
+  for (int z = 0; z < n[1]; ++z)
+    for (int x = 0; x < n[0]; ++x) {
+      double kx = kval(x, n[0], h[0]), kz = kval(z, n[1], h[1]);
+      U[(long)z * n[0] + x] = or_q2dxz_value(kx, kz, d);
+    }
+}
+
 /* Phi = Re IDFT[ U DFT(n) ] / N_total   (convolution theorem). */
 int or_dipolar_potential(const or_params *p, const double *dens, double *phi) {
   long N = nsites(p);
@@ -258,6 +283,9 @@ int or_dipolar_potential(const or_params *p, const double *dens, double *phi) {
   if (p->kernel == OR_KERNEL_DIPOLAR_3D) {
     if (p->dim != 3) { free(U); return -1; }
     or_kernel_3d(U, p->n, p->h);
+  } else if (p->kernel == OR_KERNEL_QUASI2D_XZ) {
+    if (p->dim != 2) { free(U); return -1; }
+    or_kernel_q2dxz(U, p->n, p->h, p->qd);
   } else {
     if (p->dim != 2) { free(U); return -1; }
     or_kernel_q2d(U, p->n, p->h, p->qd);

@@ -26,10 +26,11 @@
 #define OR_KERNEL_NONE 0
 #define OR_KERNEL_DIPOLAR_3D 1
 #define OR_KERNEL_QUASI2D_XY 2
+#define OR_KERNEL_QUASI2D_XZ 3  /* 2D grid in the (x, z) plane, dipoles along z in-plane */
 #define OR_MAXM 16
 
 typedef struct {
-  int dim;          /* 2 (XY plane) or 3 */
+  int dim;          /* 2 (XY or XZ plane, by kernel) or 3 */
   int n[3];         /* nx, ny, nz (nz = 1 in 2D) */
   double h[3];      /* grid spacings */
   double nu[3];     /* trap frequencies: V0 = 1/2 sum nu_a^2 x_a^2 */
@@ -37,7 +38,7 @@ typedef struct {
   double dt;        /* time step */
   int imag;         /* 1 = imaginary time (renormalised each step), 0 = real */
   int kernel;       /* OR_KERNEL_* */
-  double qd;        /* quasi-2D z-width d */
+  double qd;        /* quasi-2D width d of the transverse profile (z for XY, y for XZ) */
   int M;            /* number of trap-modulation coefficients c_1..c_M */
   double cm[OR_MAXM];
 } or_params;
@@ -57,6 +58,9 @@ int or_fftn(double complex *a, const int *dims, int ndim, int sign);
 void or_kernel_3d(double *U, const int n[3], const double h[3]);
 void or_kernel_q2d(double *U, const int n[3], const double h[3], double d);
 double or_q2d_value(double krho, double d);
+/* Quasi-2D XZ kernel on the (nz, nx) grid (n[1], h[1] hold the z axis). */
+void or_kernel_q2dxz(double *U, const int n[3], const double h[3], double d);
+double or_q2dxz_value(double kx, double kz, double d);
 
 /* Phi_d for a real density on the grid of p. */
 int or_dipolar_potential(const or_params *p, const double *dens, double *phi);

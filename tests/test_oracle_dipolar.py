@@ -156,3 +156,46 @@ def test_quasi2d_single_mode():
     U0 = oracle.q2d_value(0.0, d)
     ref = U0 * 1.0 + 0.2 * oracle.q2d_value(kx, d) * np.cos(kx * X)
     assert np.max(np.abs(phi - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("kx,kz", [(0.0, 0.4), (0.7, 0.0), (1.0, 1.0), (0.3, 2.5), (5.0, 3.0), (12.0, 20.0)])
+@pytest.mark.parametrize("d", [0.5, 1.0])
+def test_quasi2d_xz_kernel_vs_quadrature(kx, kz, d):
+    """XZ plane, dipoles along z in the plane, transverse profile in y:
+    U(kx, kz) = int dky/(2pi) (4pi/3)(3 kz^2/(kx^2 + ky^2 + kz^2) - 1) exp(-ky^2 d^2/2)."""
+    def f(ky):
+        k2 = kx * kx + ky * ky + kz * kz
+        return (4 * math.pi / 3) * (3 * kz * kz / k2 - 1) * math.exp(-ky * ky * d * d / 2) / (2 * math.pi)
+    val, _ = integrate.quad(f, -np.inf, np.inf, epsabs=1e-13, epsrel=1e-12, limit=400)
+    assert abs(oracle.q2dxz_value(kx, kz, d) - val) < 1e-10 * max(1.0, abs(val))
+
+
+@pytest.mark.parametrize("d", [0.3, 0.5, 1.0])
+def test_quasi2d_xz_identities(d):
+    """Exact consequences of the definition.  With kz = 0 the in-plane term
+    vanishes: U(kx, 0) = -(4pi/3)/(sqrt(2pi) d) for every kx.  At kx = 0, kz = k
+    the XZ integrand is 3 k^2/(k^2 + ky^2) - 1 and the XY kernel's (dipoles
+    along the integrated axis) is 3 ky^2/(k^2 + ky^2) - 1; their sum is 1, so
+    U_XZ(0, k) + U_XY(k) = (4pi/3)/(sqrt(2pi) d)."""
+    pref = (4 * math.pi / 3) / (math.sqrt(2 * math.pi) * d)
+    for kx in (0.0, 0.1, 1.0, 7.0, 40.0):
+        assert abs(oracle.q2dxz_value(kx, 0.0, d) + pref) < 1e-13 * pref
+    for k in (0.05, 0.5, 2.0, 9.0, 30.0):
+        assert abs(oracle.q2dxz_value(0.0, k, d) + oracle.q2d_value(k, d) - pref) < 1e-12 * pref
+
+
+def test_quasi2d_xz_single_modes():
+    """Fourier modes along z and along x on the (x, z) grid."""
+    n, h, d = (24, 20), (0.2, 0.3), 0.5
+    Z, X = _grid(n, h)
+    kz = 2 * math.pi * 2 / (n[1] * h[1])
+    kx = 2 * math.pi * 3 / (n[0] * h[0])
+    p = oracle.Params(dim=2, n=n, h=h, nu=(1, 1), kernel="quasi2d_xz", qd=d)
+    dens = 1.0 + 0.2 * np.cos(kz * Z) + 0.1 * np.cos(kx * X)
+    phi = oracle.dipolar_potential(p, dens)
+    U0 = oracle.q2dxz_value(0.0, 0.0, d)
+    ref = U0 + 0.2 * oracle.q2dxz_value(0.0, kz, d) * np.cos(kz * Z) + 0.1 * oracle.q2dxz_value(kx, 0.0, d) * np.cos(kx * X)
+    assert np.max(np.abs(phi - ref)) < 1e-12
+    # dipoles along z in the plane: the kernel is positive for wave vectors
+    # along the dipoles and negative across them
+    assert oracle.q2dxz_value(0.0, kz, d) > 0 > oracle.q2dxz_value(kx, 0.0, d)
