@@ -45,6 +45,12 @@ WORKLOADS = {
                     desc="adjoint real3d 128^3, h=0.15, FP32-bulk, dt=1e-3, 1000 steps, V(t)=V0(1+sum "
                          "c_m sin(m t)), c_m~U(-0.05,0.05); fidelity gradient w.r.t. c_1..c_8 and g, "
                          "checkpoint every 32 steps"),
+    "xz2d": dict(n=(512, 512), h=(0.05, 0.05), nu=(1.0, 2.0), g_prep=200.0, g=150.0, gdd=60.0, dt=5e-4,
+                 widths=(1.0, 2.0), seed=2017, prep_steps=200, kernel="quasi2d_xz", qd=0.5,
+                 metric="2D XZ split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline",
+                 desc="2D XZ plane 512x512, h=0.05, nu=(1,2), dipoles along z in the plane, quasi-2D "
+                      "XZ kernel d=0.5, g 200->150 quench, g_dd=60, dt=5e-4, real time from the "
+                      "imaginary-time ground state"),
     "imag3d": dict(n=(32, 32, 32), h=(0.25, 0.25, 0.25), nu=(1.0, 1.0, 2.0), g_prep=None, g=50.0,
                    gdd=15.0, dt=2e-3, widths=(1.0, 1.0, 2.0), seed=1601, prep_steps=0, imag=True,
                    desc="imag3d 32^3, h=0.25, nu=(1,1,2), g=50, g_dd=15, imaginary dt=0.002"),
@@ -152,10 +158,10 @@ def run_oracle_sample(wl, seconds=12.0, max_steps=3):
     import oracle
     from paper_1601_04640_gb300 import synth
     n = wl["n"]
-    p = oracle.Params(dim=3, n=n, h=wl["h"], nu=wl["nu"], g=wl["g"], gdd=wl["gdd"], dt=wl["dt"],
-                      imag=wl.get("imag", False), kernel="dipolar3d")
+    p = oracle.Params(dim=len(n), n=n, h=wl["h"], nu=wl["nu"], g=wl["g"], gdd=wl["gdd"], dt=wl["dt"],
+                      imag=wl.get("imag", False), kernel=wl.get("kernel", "dipolar3d"), qd=wl.get("qd", 0.5))
     psi = synth.gaussian_state(n, wl["h"], wl["widths"], 0.01, wl["seed"])
-    sites = n[0] * n[1] * n[2]
+    sites = int(np.prod(n))
     steps, t0 = 0, time.perf_counter()
     while steps < max_steps:
         psi = oracle.step(p, psi, steps, 1)
@@ -164,8 +170,8 @@ def run_oracle_sample(wl, seconds=12.0, max_steps=3):
             break
     dt = time.perf_counter() - t0
     return {"value": sites * steps / dt, "unit": "site-updates/s", "cores": oracle.threads(),
-            "kind": "oracle", "sample": "%d full step(s) of the %dx%dx%d workload, FP64 C oracle" % (
-                steps, n[0], n[1], n[2])}, steps, dt
+            "kind": "oracle", "sample": "%d full step(s) of the %s workload, FP64 C oracle" % (
+                steps, "x".join(str(v) for v in n))}, steps, dt
 
 
 def main():
@@ -194,8 +200,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     n = wl["n"]
-    sites = n[0] * n[1] * n[2] if n else 0
-    metric = "3D split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline"
+    sites = int(np.prod(n)) if n else 0
+    dim = len(n) if n else 3
+    metric = wl.get("metric", "3D split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline")
 
     if args.impl == "reference":
         if rank != 0:
@@ -238,10 +245,13 @@ def main():
 
     # ground state (imaginary time at g_prep), prepared once in FP32-bulk
     psi0 = synth.gaussian_state(n, wl["h"], wl["widths"], 0.01, wl["seed"])
+    kcode = {"dipolar3d": dgpe.DGPE_KERNEL_DIPOLAR_3D, "quasi2d": dgpe.DGPE_KERNEL_QUASI2D_XY,
+             "quasi2d_xz": dgpe.DGPE_KERNEL_QUASI2D_XZ}[wl.get("kernel", "dipolar3d")]
+    qd = wl.get("qd", 0.5)
     prep = None
     if wl["g_prep"] is not None and wl["prep_steps"] > 0:
-        with dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g_prep"], wl["gdd"], 2e-3, True, False,
-                         stream=stream.cuda_stream) as s:
+        with dgpe.Solver(dim, n, wl["h"], wl["nu"], wl["g_prep"], wl["gdd"], 2e-3, True, False,
+                         kernel=kcode, qd=qd, stream=stream.cuda_stream) as s:
             s.set_psi(psi0)
             s.step(wl["prep_steps"])
             prep = s.observables()
@@ -254,9 +264,13 @@ def main():
 
     forms = {}
     order = {"both": (True, False), "fp64": (True,), "fp32": (False,)}[args.forms]
+    # L2 is 129 MB: a state that fits is evicted before every timed step
+    flush = None
+    if 16 * sites < (256 << 20):
+        flush = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
     for fp64 in order:
         name = "fp64" if fp64 else "fp32_bulk"
-        S = dgpe.Solver(3, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64,
+        S = dgpe.Solver(dim, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64, kernel=kcode, qd=qd,
                         stream=stream.cuda_stream, cn=None if (args.cn == "auto" or not fp64) else args.cn)
         S.set_psi(psi0)
         S.step(args.warmup)
@@ -266,17 +280,39 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = dgpe.dgpe_kernel_launches(S.h)
-        e0.record(stream)
-        S.step(args.steps)
-        e1.record(stream)
+        if flush is None:
+            e0.record(stream)
+            S.step(args.steps)
+            e1.record(stream)
+        else:
+            # the state fits in L2: every timed step starts after a 256 MB write
+            # (outside its events) has evicted it
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for a0, a1 in evs:
+                    flush.add_(1.0)
+                    a0.record(stream)
+                    S.step(1)
+                    a1.record(stream)
         launches = dgpe.dgpe_kernel_launches(S.h) - l0
         barrier()
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
+        ms = e0.elapsed_time(e1) if flush is None else sum(a0.elapsed_time(a1) for a0, a1 in evs)
         ms_max = shard.max_over_ranks(ms)
         obs = S.observables()
         # per-pass durations (passes launched one by one, events between them)
-        passes = dgpe.dgpe_profile_steps(S.h, max(3, args.steps // 2))
+        if flush is None:
+            passes = dgpe.dgpe_profile_steps(S.h, max(3, args.steps // 2))
+        else:
+            # one profiled step per L2 flush, averaged
+            runs = []
+            for _ in range(max(3, min(args.steps, 20))):
+                with torch.cuda.stream(stream):
+                    flush.add_(1.0)
+                runs.append(dgpe.dgpe_profile_steps(S.h, 1))
+            passes = [(r0[0], sum(r[i][1] for r in runs) / len(runs), r0[2], r0[3])
+                      for i, r0 in enumerate(runs[0])]
         tot = sum(p[1] for p in passes)
         top = max(passes, key=lambda p: p[1])
         achieved = top[2] / (top[1] * 1e-3) / 1e9
@@ -338,7 +374,7 @@ def main():
     # the paper's design (separate kernels + cuFFT R2C/C2R, one thread per CN
     # line), same workload and state, timed the same way: comparison only
     plain = None
-    if not args.no_plain and not imag:
+    if not args.no_plain and not imag and dim == 3:
         try:
             from paper_1601_04640_gb300 import plain as pl
             gbuild.build_plain()
@@ -381,8 +417,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl["desc"], "grid": list(n), "sites": sites,
                    "form": "fp64" if "fp64" in forms else "fp32_bulk",
-                   "l2": "inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
-                       16 * sites >> 20, 8 * sites >> 20),
+                   "l2": ("inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
+                       16 * sites >> 20, 8 * sites >> 20)) if flush is None else
+                         "L2 flushed before every timed step (256 MB write outside the step's events); "
+                         "the state (%.1f MB FP64) fits in L2" % (16 * sites / 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
                                                       "mu": prep["mu"]}},

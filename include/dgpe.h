@@ -61,10 +61,16 @@ extern "C" {
 /* dgpe_params.kernel */
 #define DGPE_KERNEL_NONE 0
 #define DGPE_KERNEL_DIPOLAR_3D 1
-#define DGPE_KERNEL_QUASI2D_XY 2
-/* dgpe_params.plane (2D only) */
+#define DGPE_KERNEL_QUASI2D_XY 2  /* 2D XY plane, dipoles along z (normal to the plane) */
+#define DGPE_KERNEL_QUASI2D_XZ 3  /* 2D XZ plane, dipoles along z (in the plane):
+                                     U(kx, kz) = (4pi/3)/(sqrt(2pi) d) [3 sqrt(pi/2)
+                                     (kz^2 d/krho) erfcx(krho d/sqrt2) - 1], the 3D
+                                     kernel averaged over the y-profile
+                                     exp(-y^2/d^2)/(sqrt(pi) d) */
+/* dgpe_params.plane (2D only).  For XZ the second axis is z: n[1], h[1] and
+   nu[1] describe z, and psi is stored [z][x]. */
 #define DGPE_PLANE_XY 0
-#define DGPE_PLANE_XZ 1         /* returns DGPE_EUNSUPPORTED */
+#define DGPE_PLANE_XZ 1
 /* dgpe_params.flags */
 #define DGPE_FLAG_NO_GRAPH 1u   /* launch the passes directly instead of
                                    replaying a captured CUDA graph */
@@ -89,7 +95,8 @@ typedef struct dgpe_params {
   int mode;         /* DGPE_IMAG or DGPE_REAL */
   int precision;    /* DGPE_FP64 or DGPE_FP32_BULK */
   int kernel;       /* DGPE_KERNEL_* (DIPOLAR_3D needs dim 3, QUASI2D_XY dim 2) */
-  double qd;        /* quasi-2D z-width d > 0 (QUASI2D_XY only) */
+  double qd;        /* quasi-2D width d > 0 of the transverse profile (z for
+                       QUASI2D_XY, y for QUASI2D_XZ) */
   unsigned flags;   /* DGPE_FLAG_* */
 } dgpe_params;
 

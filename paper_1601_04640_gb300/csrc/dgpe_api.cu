@@ -41,9 +41,8 @@ extern "C" int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_t *out)
   *out = nullptr;
   if (!p) return fail(nullptr, DGPE_EINVAL, "params is NULL");
   if (p->dim != 2 && p->dim != 3) return fail(nullptr, DGPE_EINVAL, "dim must be 2 or 3");
-  if (p->dim == 2 && p->plane == DGPE_PLANE_XZ)
-    return fail(nullptr, DGPE_EUNSUPPORTED, "the 2D XZ plane is not supported");
-  if (p->dim == 2 && p->plane != DGPE_PLANE_XY) return fail(nullptr, DGPE_EINVAL, "bad plane");
+  if (p->dim == 2 && p->plane != DGPE_PLANE_XY && p->plane != DGPE_PLANE_XZ)
+    return fail(nullptr, DGPE_EINVAL, "bad plane");
   for (int a = 0; a < p->dim; ++a) {
     if (!(p->h[a] > 0.0) || !std::isfinite(p->h[a])) return fail(nullptr, DGPE_EINVAL, "spacing must be > 0");
     if (!(p->nu[a] >= 0.0) || !std::isfinite(p->nu[a])) return fail(nullptr, DGPE_EINVAL, "trap frequency must be >= 0");
@@ -56,9 +55,11 @@ extern "C" int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_t *out)
   if (p->precision != DGPE_FP64 && p->precision != DGPE_FP32_BULK) return fail(nullptr, DGPE_EINVAL, "bad precision");
   if (p->kernel == DGPE_KERNEL_DIPOLAR_3D && p->dim != 3)
     return fail(nullptr, DGPE_EINVAL, "the 3D dipolar kernel needs dim 3");
-  if (p->kernel == DGPE_KERNEL_QUASI2D_XY && (p->dim != 2 || !(p->qd > 0.0)))
-    return fail(nullptr, DGPE_EINVAL, "the quasi-2D kernel needs dim 2 and qd > 0");
-  if (p->kernel < 0 || p->kernel > 2) return fail(nullptr, DGPE_EINVAL, "bad kernel");
+  if (p->kernel == DGPE_KERNEL_QUASI2D_XY && (p->dim != 2 || p->plane != DGPE_PLANE_XY || !(p->qd > 0.0)))
+    return fail(nullptr, DGPE_EINVAL, "the quasi-2D XY kernel needs dim 2, the XY plane and qd > 0");
+  if (p->kernel == DGPE_KERNEL_QUASI2D_XZ && (p->dim != 2 || p->plane != DGPE_PLANE_XZ || !(p->qd > 0.0)))
+    return fail(nullptr, DGPE_EINVAL, "the quasi-2D XZ kernel needs dim 2, the XZ plane and qd > 0");
+  if (p->kernel < 0 || p->kernel > 3) return fail(nullptr, DGPE_EINVAL, "bad kernel");
   dgpe_solver *h = new (std::nothrow) dgpe_solver();
   if (!h) return fail(nullptr, DGPE_ENOMEM, "host allocation failed");
   h->stream = (cudaStream_t)cuda_stream;

@@ -471,6 +471,15 @@ template <typename R> struct EngineT : Engine {
             const double qz = wavenumber(kz, nz, p.h[2]);
             const double k2 = qx * qx + qy * qy + qz * qz;
             u = (k2 == 0.0) ? 0.0 : (4.0 * M_PI / 3.0) * (3.0 * qz * qz / k2 - 1.0);
+          } else if (p.kernel == DGPE_KERNEL_QUASI2D_XZ) {
+            // (x, z) plane (the second axis is z), dipoles along z in the
+            // plane, Gaussian y-profile exp(-y^2/d^2)/(sqrt(pi) d):
+            // U2 = (4pi/3)/(sqrt(2pi) d) [3 sqrt(pi/2) (kz^2 d/krho) erfcx(krho d/sqrt2) - 1]
+            const double d = p.qd, qz = qy, krho = std::sqrt(qx * qx + qz * qz);
+            const double pref = (4.0 * M_PI / 3.0) / (std::sqrt(2.0 * M_PI) * d);
+            u = (krho == 0.0) ? -pref
+                              : pref * (3.0 * std::sqrt(M_PI / 2.0) * (qz * qz * d / krho) *
+                                            host_erfcx(krho * d / std::sqrt(2.0)) - 1.0);
           } else {
             // dipoles along z, Gaussian z-profile exp(-z^2/d^2)/(sqrt(pi) d):
             // U2 = (4pi/3)/(sqrt(2pi) d) [2 - 3 sqrt(pi/2) q erfcx(q/sqrt2)], q = k d

@@ -30,6 +30,7 @@ DGPE_FP32_BULK = 1
 DGPE_KERNEL_NONE = 0
 DGPE_KERNEL_DIPOLAR_3D = 1
 DGPE_KERNEL_QUASI2D_XY = 2
+DGPE_KERNEL_QUASI2D_XZ = 3
 DGPE_PLANE_XY = 0
 DGPE_PLANE_XZ = 1
 DGPE_FLAG_NO_GRAPH = 1
@@ -130,11 +131,15 @@ def _check(rc, h=None):
 
 
 def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                kernel=None, qd=0.5, graph=True, cn=None):
-    """cn: None (automatic), "serial" or "chunked" (FP64 Crank-Nicolson form)."""
+                kernel=None, qd=0.5, graph=True, cn=None, plane=None):
+    """cn: None (automatic), "serial" or "chunked" (FP64 Crank-Nicolson form).
+    plane (2D): "xy" or "xz"; default XZ for the XZ kernel, else XY.  For XZ the
+    second axis is z: n, h, nu = (nx, nz), (hx, hz), (nu_x, nu_z)."""
     p = dgpe_params()
     p.dim = dim
-    p.plane = DGPE_PLANE_XY
+    if plane is None:
+        plane = "xz" if kernel == DGPE_KERNEL_QUASI2D_XZ else "xy"
+    p.plane = {"xy": DGPE_PLANE_XY, "xz": DGPE_PLANE_XZ}[plane]
     nn = list(n) + [1] * (3 - len(n))
     hh = list(h) + [1.0] * (3 - len(h))
     vv = list(nu) + [0.0] * (3 - len(nu))

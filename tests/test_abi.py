@@ -68,11 +68,14 @@ def test_argument_errors_without_device(lib):
     with pytest.raises(dgpe.DgpeError) as e:
         dgpe.dgpe_create(p)
     assert e.value.code == dgpe.DGPE_EUNSUPPORTED
-    p = dgpe.make_params(2, (32, 32), (0.25,) * 2, (1, 1))
-    p.plane = dgpe.DGPE_PLANE_XZ
-    with pytest.raises(dgpe.DgpeError) as e:
-        dgpe.dgpe_create(p)
-    assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+    # the quasi-2D kernels must match the plane; an unknown plane is an error
+    for kernel, plane in ((dgpe.DGPE_KERNEL_QUASI2D_XY, dgpe.DGPE_PLANE_XZ),
+                          (dgpe.DGPE_KERNEL_QUASI2D_XZ, dgpe.DGPE_PLANE_XY), (dgpe.DGPE_KERNEL_NONE, 7)):
+        p = dgpe.make_params(2, (32, 32), (0.25,) * 2, (1, 1), kernel=kernel)
+        p.plane = plane
+        with pytest.raises(dgpe.DgpeError) as e:
+            dgpe.dgpe_create(p)
+        assert e.value.code == dgpe.DGPE_EINVAL
     p = dgpe.make_params(2, (32, 32), (0.25,) * 2, (1, 1), kernel=dgpe.DGPE_KERNEL_DIPOLAR_3D)
     with pytest.raises(dgpe.DgpeError) as e:
         dgpe.dgpe_create(p)

@@ -31,9 +31,9 @@ def rel_l2(a, b):
 
 
 def make_case(dim, n, h, nu, g, gdd, dt, imag, kernel=None, seed=1601, noise=0.01, widths=None):
-    kname = {None: "dipolar3d" if dim == 3 else "quasi2d", "none": "none"}[kernel]
+    kname = {None: "dipolar3d" if dim == 3 else "quasi2d", "none": "none", "xz": "quasi2d_xz"}[kernel]
     op = oracle.Params(dim=dim, n=n, h=h, nu=nu, g=g, gdd=gdd, dt=dt, imag=imag, kernel=kname, qd=0.5)
-    kc = {None: None, "none": dgpe.DGPE_KERNEL_NONE}[kernel]
+    kc = {None: None, "none": dgpe.DGPE_KERNEL_NONE, "xz": dgpe.DGPE_KERNEL_QUASI2D_XZ}[kernel]
     psi0 = synth.gaussian_state(n, h, widths or nu, noise, seed)
     return op, kc, psi0
 
@@ -350,3 +350,33 @@ def test_launch_counter_and_operation_model():
         for f in flops[-3:]:
             assert f == 28.0 * 64 ** 3
         assert all(f > 0 for f in flops)
+
+
+def test_dipolar_potential_quasi2d_xz():
+    """XZ plane (second axis z), dipoles along z in the plane."""
+    n, h, nu = (96, 64), (0.2, 0.25), (1.0, 1.5)
+    psi0 = synth.gaussian_state(n, h, (1.0, 1.5), 0.05, 11)
+    op = oracle.Params(dim=2, n=n, h=h, nu=nu, kernel="quasi2d_xz", qd=0.5)
+    ref = oracle.dipolar_potential(op, np.abs(psi0) ** 2)
+    for fp64, tol in ((True, 1e-12), (False, 1e-5)):
+        with dgpe.Solver(2, n, h, nu, 10, 5, 1e-3, False, fp64, kernel=dgpe.DGPE_KERNEL_QUASI2D_XZ) as s:
+            s.set_psi(psi0)
+            phi = s.dipolar_potential()
+        e = rel_l2(phi, ref)
+        print("fp64" if fp64 else "fp32", "Phi rel L2", e)
+        assert e < tol
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("n", [(64, 96), (128, 64), (160, 160)])
+def test_step_parity_2d_xz(fp64, imag, n):
+    h, nu = (0.2, 0.25), (1.0, 1.5)
+    op, kc, psi0 = make_case(2, n, h, nu, 80.0, 40.0, 1e-3, imag, kernel="xz")
+    psi, obs = gpu_run(2, n, h, nu, 80.0, 40.0, 1e-3, imag, fp64, kc, psi0, 10)
+    ref = oracle.step(op, psi0, 0, 10)
+    e = rel_l2(psi, ref)
+    r = oracle.observables(op, ref, 10)
+    print("rel L2", e, "mu", obs["mu"], r["mu"])
+    assert e < TOL_PSI[fp64]
+    assert abs(obs["mu"] - r["mu"]) <= TOL_MU[fp64] * abs(r["mu"])
