@@ -408,6 +408,15 @@ def main():
         import oracle.build
         oracle.build.build()
         cpu, _, _ = run_oracle_sample(wl)
+        # the paper's baseline is one CPU core: the same oracle on one thread
+        import oracle
+        allc = oracle.threads()
+        oracle.set_threads(1)
+        try:
+            one, _, _ = run_oracle_sample(wl, seconds=15.0, max_steps=1)
+        finally:
+            oracle.set_threads(allc)
+        cpu["single_core"] = {k: one[k] for k in ("value", "cores", "sample")}
     a = forms["fp64"] if "fp64" in forms else forms["fp32_bulk"]
     b = forms.get("fp32_bulk") if "fp64" in forms else None
     line = {
