@@ -105,11 +105,14 @@ def load():
         lib.or_trap_scale.argtypes = [P, C.c_double]
         lib.or_trap_scale.restype = C.c_double
         lib.or_nonlinear.argtypes = [P, cp, C.c_long]
+        lib.or_nonlinear_frac.argtypes = [P, cp, C.c_double, C.c_double]
         lib.or_thomas.argtypes = [cp, cp, cp, cp, cp, C.c_int]
         lib.or_cn_axis.argtypes = [P, cp, C.c_int]
         lib.or_normalize.argtypes = [P, cp]
         lib.or_step.argtypes = [P, cp, C.c_long]
         lib.or_run.argtypes = [P, cp, C.c_long, C.c_long]
+        lib.or_step_strang.argtypes = [P, cp, C.c_long]
+        lib.or_run_strang.argtypes = [P, cp, C.c_long, C.c_long]
         lib.or_observables.argtypes = [P, cp, C.c_long, C.POINTER(_Obs)]
         lib.or_step_adjoint.argtypes = [P, cp, cp, C.c_long, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]
@@ -227,12 +230,29 @@ def normalize(p: Params, psi):
     return psi
 
 
-def step(p: Params, psi, step0=0, nsteps=1):
-    """Advance nsteps steps starting at step index step0; returns a new array."""
+def nonlinear_frac(p: Params, psi, t, f):
+    """Exponential substep over f dt with the trap at time t."""
+    psi = _c128(psi)
+    if load().or_nonlinear_frac(C.byref(p._c()), psi, float(t), float(f)):
+        raise ValueError("nonlinear substep failed")
+    return psi
+
+
+SPLITS = ("lie", "strang")
+
+
+def step(p: Params, psi, step0=0, nsteps=1, split="lie"):
+    """Advance nsteps steps starting at step index step0; returns a new array.
+
+    split "lie": the paper's first-order splitting (exponential, then CN along
+    x, y, z); "strang": half exponential, CN, half exponential (real time)."""
     psi = _c128(psi)
     if psi.shape != p.shape():
         raise ValueError("psi shape %s != %s" % (psi.shape, p.shape()))
-    if load().or_run(C.byref(p._c()), psi, int(step0), int(nsteps)):
+    if split not in SPLITS:
+        raise ValueError("split must be one of %s" % (SPLITS,))
+    run = load().or_run if split == "lie" else load().or_run_strang
+    if run(C.byref(p._c()), psi, int(step0), int(nsteps)):
         raise ValueError("step failed")
     return psi
 

@@ -330,8 +330,10 @@ double or_trap_scale(const or_params *p, double t) {
 
 /* ------------------------------------------------------------- substeps */
 
-/* psi <- exp(-kappa dt (s V0 + g n + g_dd Phi)) psi, n = |psi|^2 at entry. */
-int or_nonlinear(const or_params *p, double complex *psi, long step) {
+/* psi <- exp(-kappa f dt (s(t) V0 + g n + g_dd Phi)) psi, n = |psi|^2 at
+ * entry: the exponential substep over the fraction f of a time step with the
+ * trap evaluated at time t. */
+int or_nonlinear_frac(const or_params *p, double complex *psi, double t, double f) {
   long N = nsites(p);
   double *dens = (double *)malloc(sizeof(double) * N);
   double *phi = (double *)malloc(sizeof(double) * N);
@@ -340,10 +342,11 @@ int or_nonlinear(const or_params *p, double complex *psi, long step) {
   int rc = or_dipolar_potential(p, dens, phi);
   if (rc) { free(dens); free(phi); free(V0); return rc; }
   or_trap(p, V0);
-  double s = or_trap_scale(p, (double)step * p->dt);
+  double s = or_trap_scale(p, t);
+  double fdt = f * p->dt;
 #pragma omp parallel for schedule(static)
   for (long i = 0; i < N; ++i) {
-    double th = p->dt * (s * V0[i] + p->g * dens[i] + p->gdd * phi[i]);
+    double th = fdt * (s * V0[i] + p->g * dens[i] + p->gdd * phi[i]);
     if (p->imag)
       psi[i] *= exp(-th);
     else
@@ -353,6 +356,11 @@ int or_nonlinear(const or_params *p, double complex *psi, long step) {
   free(phi);
   free(V0);
   return 0;
+}
+
+/* The exponential substep of step `step` (a full dt at t = step dt). */
+int or_nonlinear(const or_params *p, double complex *psi, long step) {
+  return or_nonlinear_frac(p, psi, (double)step * p->dt, 1.0);
 }
 
 /* Thomas algorithm for a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i. */
@@ -454,6 +462,30 @@ int or_step(const or_params *p, double complex *psi, long step) {
   or_cn_axis(p, psi, 1);
   if (p->dim == 3) or_cn_axis(p, psi, 2);
   if (p->imag) or_normalize(p, psi);
+  return 0;
+}
+
+/* Second-order (Strang) splitting of step `step`, real time:
+ *   psi <- E(dt/2, t_{k+1}) C_z C_y C_x E(dt/2, t_k) psi,  t_k = step dt,
+ * where E(f dt, t) is the exponential substep with the density of its own
+ * input, so the closing half uses the density after the Crank-Nicolson
+ * substeps.  (The paper uses first-order splitting; this symmetric variant is
+ * second order in dt.)  Returns -3 in imaginary time. */
+int or_step_strang(const or_params *p, double complex *psi, long step) {
+  if (p->imag) return -3;
+  int rc = or_nonlinear_frac(p, psi, (double)step * p->dt, 0.5);
+  if (rc) return rc;
+  or_cn_axis(p, psi, 0);
+  or_cn_axis(p, psi, 1);
+  if (p->dim == 3) or_cn_axis(p, psi, 2);
+  return or_nonlinear_frac(p, psi, (double)(step + 1) * p->dt, 0.5);
+}
+
+int or_run_strang(const or_params *p, double complex *psi, long step0, long nsteps) {
+  for (long s = 0; s < nsteps; ++s) {
+    int rc = or_step_strang(p, psi, step0 + s);
+    if (rc) return rc;
+  }
   return 0;
 }
 

@@ -71,6 +71,7 @@ double or_trap_scale(const or_params *p, double t);
 
 /* Substeps. */
 int or_nonlinear(const or_params *p, double complex *psi, long step);
+int or_nonlinear_frac(const or_params *p, double complex *psi, double t, double f);
 void or_thomas(const double complex *a, const double complex *b,
                const double complex *c, const double complex *d,
                double complex *x, int n);
@@ -78,6 +79,9 @@ void or_cn_axis(const or_params *p, double complex *psi, int axis);
 void or_normalize(const or_params *p, double complex *psi);
 int or_step(const or_params *p, double complex *psi, long step);
 int or_run(const or_params *p, double complex *psi, long step0, long nsteps);
+/* second-order (Strang) splitting, real time only (-3 in imaginary time) */
+int or_step_strang(const or_params *p, double complex *psi, long step);
+int or_run_strang(const or_params *p, double complex *psi, long step0, long nsteps);
 int or_observables(const or_params *p, const double complex *psi, long step,
                    or_obs *o);
 
