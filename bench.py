@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the cuFFT comparison step")
+    ap.add_argument("--no-strang", action="store_true", help="skip the second-order splitting leg")
     ap.add_argument("--cn", default="auto", choices=["auto", "serial", "chunked"],
                     help="Crank-Nicolson solve form of the FP64 form (auto: the library's default "
                          "for the grid size); the FP32 form always uses the chunk-parallel solve")
@@ -371,6 +372,37 @@ def main():
         S.close()
         forms[name] = f
 
+    # second-order (Strang) splitting on the same workload and state: one
+    # dgpe_step(K) call runs K first-order steps between two exponential
+    # passes over -dt/2 and +dt/2
+    strang = None
+    if not imag and not args.no_strang:
+        if flush is not None:
+            strang = {"unavailable": "timed on states larger than L2 only (one call of K steps)"}
+        else:
+            strang = {}
+            for fp64 in order:
+                name = "fp64" if fp64 else "fp32_bulk"
+                with dgpe.Solver(dim, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], False, fp64,
+                                 kernel=kcode, qd=qd, stream=stream.cuda_stream, split="strang",
+                                 cn=None if (args.cn == "auto" or not fp64) else args.cn) as S2:
+                    S2.set_psi(psi0)
+                    S2.step(args.warmup)
+                    barrier()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    l0 = dgpe.dgpe_kernel_launches(S2.h)
+                    e0.record(stream)
+                    S2.step(args.steps)
+                    e1.record(stream)
+                    barrier()
+                    launches = dgpe.dgpe_kernel_launches(S2.h) - l0
+                    ms = shard.max_over_ranks(e0.elapsed_time(e1))
+                strang[name] = {"value": world * sites * args.steps / (ms * 1e-3),
+                                "ms_per_step": ms / args.steps,
+                                "time_vs_first_order": (ms / args.steps) / forms[name]["ms_per_step"],
+                                "gpu_launches": launches}
+
     # the paper's design (separate kernels + cuFFT R2C/C2R, one thread per CN
     # line), same workload and state, timed the same way: comparison only
     plain = None
@@ -440,6 +472,7 @@ def main():
         "clocks": a["clocks"], "observables_after": a["observables_after"],
         "fp32_bulk": b,
         "cufft_plain_step": plain,
+        "strang_split": strang,
         "speedup_fp32_bulk_vs_fp64": (b["value"] / a["value"]) if b else None,
         "source_hash": source_hash(),
     }

@@ -80,6 +80,17 @@ extern "C" {
                                    form returns DGPE_EUNSUPPORTED */
 #define DGPE_FLAG_CN_CHUNKED 4u /* FP64 form: always use the chunk-parallel
                                    CN solve (exclusive with CN_SERIAL) */
+#define DGPE_FLAG_STRANG 8u     /* real time: second-order (Strang) splitting,
+                                   one step = E(dt/2, t_{k+1}) C_z C_y C_x
+                                   E(dt/2, t_k), the closing half with the
+                                   density after the CN substeps (the paper's
+                                   step is first order: E(dt, t_k) then CN).
+                                   dgpe_step(h, n) runs it as n first-order
+                                   steps between an exponential substep over
+                                   -dt/2 and one over +dt/2 (|psi| is unchanged
+                                   by the exponential in real time).  Imaginary
+                                   time, the reverse step and the batched form
+                                   return DGPE_EUNSUPPORTED. */
 
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */
@@ -136,7 +147,8 @@ int dgpe_get_psi(dgpe_t h, double *psi, size_t n_sites);
 int dgpe_set_psi_device(dgpe_t h, const void *psi, size_t n_sites, int fp64);
 int dgpe_get_psi_device(dgpe_t h, void *psi, size_t n_sites, int fp64);
 
-/* Advance n >= 0 steps (graph replays).  Asynchronous. */
+/* Advance n >= 0 steps (graph replays; with DGPE_FLAG_STRANG, an exponential
+ * pass over -dt/2 before them and one over +dt/2 after them).  Asynchronous. */
 int dgpe_step(dgpe_t h, int n);
 
 /* norm, mu, energy, rms sizes of the current state in FP64 (calcmuen,

@@ -60,6 +60,8 @@ extern "C" int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_t *out)
   if (p->kernel == DGPE_KERNEL_QUASI2D_XZ && (p->dim != 2 || p->plane != DGPE_PLANE_XZ || !(p->qd > 0.0)))
     return fail(nullptr, DGPE_EINVAL, "the quasi-2D XZ kernel needs dim 2, the XZ plane and qd > 0");
   if (p->kernel < 0 || p->kernel > 3) return fail(nullptr, DGPE_EINVAL, "bad kernel");
+  if ((p->flags & DGPE_FLAG_STRANG) && p->mode != DGPE_REAL)
+    return fail(nullptr, DGPE_EUNSUPPORTED, "Strang splitting is defined for real time");
   dgpe_solver *h = new (std::nothrow) dgpe_solver();
   if (!h) return fail(nullptr, DGPE_ENOMEM, "host allocation failed");
   h->stream = (cudaStream_t)cuda_stream;

@@ -277,6 +277,11 @@ extern "C" int dgpe_batch_create(const dgpe_params *ps, int count, void *cuda_st
       delete b;
       return DGPE_EUNSUPPORTED;
     }
+    if (p.flags & DGPE_FLAG_STRANG) {
+      g_batch_err = "batch problems use first-order splitting";
+      delete b;
+      return DGPE_EUNSUPPORTED;
+    }
     p.flags |= DGPE_FLAG_NO_GRAPH;
     if (p.n[0] < 32 || p.n[0] > 512 || !(p.h[0] > 0.0) || !(p.h[1] > 0.0) || !(p.dt > 0.0) ||
         (p.mode != DGPE_IMAG && p.mode != DGPE_REAL) || !(p.qd > 0.0)) {

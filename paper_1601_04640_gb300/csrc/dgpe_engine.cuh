@@ -226,6 +226,7 @@ template <typename R> struct EngineT : Engine {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
+  bool strang = false;  // second-order splitting (real time)
 
   ~EngineT() override {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -406,6 +407,7 @@ template <typename R> struct EngineT : Engine {
     if ((rc = set_smem_attrs())) return rc;
     DGPE_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     use_graph = !(p.flags & DGPE_FLAG_NO_GRAPH);
+    strang = (p.flags & DGPE_FLAG_STRANG) != 0;
     if (use_graph && (rc = capture())) return rc;
     (void)user;
     return DGPE_OK;
@@ -641,7 +643,7 @@ template <typename R> struct EngineT : Engine {
     A.tw = tw[0]; A.twf = twf[0]; A.twi = twi[0]; A.vx = vt[0]; A.vy = vt[1]; A.vz = vt[2]; A.cntab = cntab[0];
     A.pl = plx; A.nx = nx; A.ny = ny; A.nrows = nrows; A.px = px; A.LP = x_LP;
     A.pitchz = x_pitchz; A.pitch = x_pitch; A.TPL = x_TPL; A.C = x_C;
-    A.imag = imag; A.has_dip = has_dip ? 1 : 0; A.tau = tau[0];
+    A.imag = imag; A.has_dip = has_dip ? 1 : 0; A.tau = tau[0]; A.dtf = 1.0;
     return A;
   }
   SArgs<R> sargs(const FtCfg &f) const {
@@ -724,10 +726,12 @@ template <typename R> struct EngineT : Engine {
     return DGPE_OK;
   }
   // mode 0: step pass on psi; 1: Phi_d into phi_out; 2: CN_x (conjugated) on
-  // buf; 3: step pass without CN_x (the line-serial CN_x pass follows)
-  int launch_p1(int mode, cudaStream_t s, Cx *buf = nullptr, R *phi_out = nullptr) {
+  // buf; 3: step pass without CN_x (the line-serial CN_x pass follows), its
+  // exponential over the fraction dtf of dt
+  int launch_p1(int mode, cudaStream_t s, Cx *buf = nullptr, R *phi_out = nullptr, double dtf = 1.0) {
     if (mode == 2 && cn_serial) return launch_lines(0, false, s, buf, true);
     XArgs<R> A = xargs();
+    A.dtf = dtf;
     if (buf) A.psi = buf;
     if (phi_out) A.phi_out = phi_out;
     if (mode == 2) {
@@ -803,6 +807,17 @@ template <typename R> struct EngineT : Engine {
       if (rc) return rc;
     }
     return DGPE_OK;
+  }
+  // Exponential substep alone over f dt at the current time (Phi_d of the
+  // current density first): the ends of a run of Strang steps.  In real time
+  // the substep leaves |psi| unchanged, so n Strang steps
+  //   E(dt/2, t_{k+1}) C E(dt/2, t_k)
+  // telescope into E(-dt/2, t_0) [C E(dt, t_k)]_{k=0..n-1} E(dt/2, t_n): the n
+  // first-order steps with one half-step pass before and after them.
+  int launch_exp_only(double f, cudaStream_t s) {
+    int rc;
+    if (has_dip && (rc = launch_dipolar_chain(s))) return rc;
+    return launch_p1(3, s, nullptr, nullptr, f);
   }
   const char *pass_name(int i) const override {
     static const char *names[] = {"dens_r2c_x", "fft_y", "fft_z_u_ifft_z", "ifft_y",
@@ -936,16 +951,18 @@ template <typename R> struct EngineT : Engine {
 
   // ------------------------------------------------------------ API calls
   int step(int n, cudaStream_t s) override {
+    int rc;
+    if (strang && n > 0 && (rc = launch_exp_only(-0.5, s))) return rc;
     for (int i = 0; i < n; ++i) {
       if (use_graph) {
         DGPE_CK(cudaGraphLaunch(gexec, s));
         nlaunch += launches_per_step();
       }
       else {
-        int rc = launch_step(s);
-        if (rc) return rc;
+        if ((rc = launch_step(s))) return rc;
       }
     }
+    if (strang && n > 0 && (rc = launch_exp_only(0.5, s))) return rc;
     return DGPE_OK;
   }
   int reset_scale(cudaStream_t s) {
@@ -1067,6 +1084,7 @@ template <typename R> struct EngineT : Engine {
   }
   int set_mode(int mode, cudaStream_t s) override {
     if (mode != DGPE_IMAG && mode != DGPE_REAL) { err = "bad mode"; return DGPE_EINVAL; }
+    if (strang && mode == DGPE_IMAG) { err = "Strang splitting is defined for real time"; return DGPE_EUNSUPPORTED; }
     // fold the lazy scale into psi, then rebuild the CN tables and the graph
     k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, nsites);
     launched(1);
@@ -1143,6 +1161,7 @@ template <typename R> struct EngineT : Engine {
   int step_adjoint(const void *psi_in, void *G, long long st, double *dg, double *dc,
                    cudaStream_t s) override {
     if (imag) { err = "the reverse step is defined for real time"; return DGPE_EUNSUPPORTED; }
+    if (strang) { err = "the reverse step is defined for first-order splitting"; return DGPE_EUNSUPPORTED; }
     int rc = adj_alloc();
     if (rc) return rc;
     DGPE_CK(cudaMemsetAsync(adj_acc, 0, 17 * sizeof(double), s));
@@ -1160,6 +1179,7 @@ template <typename R> struct EngineT : Engine {
   int fidelity_gradient(const double *psi0, const double *target, int nsteps, int every,
                         double *F, double *dFdg, double *dFdc, cudaStream_t s) override {
     if (imag) { err = "the reverse step is defined for real time"; return DGPE_EUNSUPPORTED; }
+    if (strang) { err = "the reverse step is defined for first-order splitting"; return DGPE_EUNSUPPORTED; }
     if (nsteps < 1 || every < 1) { err = "nsteps and every must be >= 1"; return DGPE_EINVAL; }
     int rc = adj_alloc();
     if (rc) return rc;

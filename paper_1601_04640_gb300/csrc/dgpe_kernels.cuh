@@ -50,6 +50,7 @@ template <typename R> struct XArgs {  // x-line passes
   int pitchz, pitch, TPL, C;
   int imag, has_dip;
   double tau;
+  double dtf;  // fraction of dt taken by the exponential substep (1: a full step)
 };
 
 template <typename R> struct SArgs {  // strided FFT passes over the spectrum
@@ -337,11 +338,11 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       pt[L * P + a + a / CL] = buf[i];
     }
   }
-  if (t == 0) s_dts = trap_dts(A.prm, *A.step);
+  if (t == 0) s_dts = trap_dts(A.prm, *A.step) * A.dtf;
   __syncthreads();
   const R dts = (R)s_dts;
-  const R gdt = (R)(A.prm[PRM_DT] * A.prm[PRM_G]);
-  const R gdddt = (R)(A.prm[PRM_DT] * A.prm[PRM_GDD]);
+  const R gdt = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_G]);
+  const R gdddt = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_GDD]);
   const R sc = (R)A.prm[PRM_SC];
   const int imag = A.imag;
   constexpr bool DIRECT = (sizeof(R) == 8);  // FP64: the direct (scaled) phase factor in real time
@@ -397,7 +398,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       apply_e(2 * l + 1, a, v.y);
     };
     tile_fft<R, EPT, true, false, PW, POW2, FMA>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store, rt);
-  } else if (MODE == 0) {
+  } else if (MODE == 0 || MODE == 3) {
     for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
   }

@@ -80,6 +80,11 @@ def test_argument_errors_without_device(lib):
     with pytest.raises(dgpe.DgpeError) as e:
         dgpe.dgpe_create(p)
     assert e.value.code == dgpe.DGPE_EINVAL
+    # second-order splitting is a real-time option
+    p = dgpe.make_params(3, (32, 32, 32), (0.25,) * 3, (1, 1, 2), imag=True, split="strang")
+    with pytest.raises(dgpe.DgpeError) as e:
+        dgpe.dgpe_create(p)
+    assert e.value.code == dgpe.DGPE_EUNSUPPORTED
 
 
 def test_product_path_does_not_reference_the_oracle():

@@ -380,3 +380,87 @@ def test_step_parity_2d_xz(fp64, imag, n):
     print("rel L2", e, "mu", obs["mu"], r["mu"])
     assert e < TOL_PSI[fp64]
     assert abs(obs["mu"] - r["mu"]) <= TOL_MU[fp64] * abs(r["mu"])
+
+
+def test_step_parity_contact_only_line_serial_cn():
+    """No dipolar term with the separate line-serial CN_x pass: the x-line pass
+    then applies the exponential without a C2R in front of it."""
+    for dim, n, h, nu in ((3, (32, 48, 40), (0.25, 0.2, 0.22), (1.0, 1.3, 0.9)),
+                          (2, (64, 96), (0.2, 0.15), (1.0, 1.4))):
+        for imag in (True, False):
+            op, kc, psi0 = make_case(dim, n, h, nu, 60.0, 0.0, 2e-3, imag, kernel="none")
+            psi, obs = gpu_run(dim, n, h, nu, 60.0, 0.0, 2e-3, imag, True, kc, psi0, 10, cn="serial")
+            ref = oracle.step(op, psi0, 0, 10)
+            e = rel_l2(psi, ref)
+            print(dim, "imag" if imag else "real", "rel L2", e)
+            assert e < TOL_PSI[True]
+
+
+# (dim, n, h, nu, fp64, kernel, cn, graph)
+STRANG_CASES = [
+    (3, (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0), True, None, None, True),
+    (3, (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0), False, None, None, True),
+    (3, (64, 32, 128), (0.2, 0.3, 0.1), (1.0, 1.3, 0.8), True, None, "serial", True),
+    (3, (96, 160, 48), (0.2, 0.15, 0.3), (1.0, 1.2, 1.5), False, None, None, False),
+    (3, (32, 48, 40), (0.25, 0.2, 0.22), (1.0, 1.3, 0.9), True, "none", "serial", True),
+    (2, (64, 32), (0.2, 0.3), (1.0, 1.5), True, None, None, True),
+    (2, (96, 64), (0.2, 0.25), (1.0, 1.5), False, "xz", None, True),
+]
+
+
+@pytest.mark.parametrize("case", range(len(STRANG_CASES)))
+def test_step_parity_strang(case):
+    """Second-order splitting: dgpe_step runs n first-order steps between
+    exponential passes over -dt/2 and +dt/2; the oracle takes n literal
+    E(dt/2, t_k+1) C E(dt/2, t_k) steps.  Two calls (3 + 4 steps), modulated
+    trap; the first-order result differs from both by more than ten times
+    the tolerance and a hundred times the measured error."""
+    dim, n, h, nu, fp64, kernel, cn, graph = STRANG_CASES[case]
+    g, gdd, dt, cm = 50.0, (0.0 if kernel == "none" else 15.0), 2e-3, [0.5, 0.0, 0.3]
+    op, kc, psi0 = make_case(dim, n, h, nu, g, gdd, dt, False, kernel=kernel)
+    op.cm = cm
+    with dgpe.Solver(dim, n, h, nu, g, gdd, dt, False, fp64, kernel=kc, cn=cn, graph=graph,
+                     split="strang") as s:
+        s.set_psi(psi0)
+        s.set_trap_modulation(cm)
+        s.step(3)
+        s.step(0)
+        s.step(4)
+        psi = s.get_psi()
+        assert s.time() == 7
+    ref = oracle.step(op, psi0, 0, 7, split="strang")
+    e = rel_l2(psi, ref)
+    d = rel_l2(oracle.step(op, psi0, 0, 7), ref)
+    print("rel L2", e, "first-order vs second-order", d)
+    assert e < TOL_PSI[fp64]
+    assert d > 10 * TOL_PSI[fp64] and d > 100 * e
+
+
+def test_strang_launches_and_refusals():
+    n, h, nu = (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0)
+    with dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, False, True, split="strang") as s:
+        s.set_psi(synth.gaussian_state(n, h, nu, 0.01, 5))
+        lps = dgpe.dgpe_launches_per_step(s.h)
+        l0 = dgpe.dgpe_kernel_launches(s.h)
+        s.step(0)
+        assert dgpe.dgpe_kernel_launches(s.h) == l0
+        s.step(3)
+        # two exponential passes, each after the four passes of the dipolar chain
+        assert dgpe.dgpe_kernel_launches(s.h) - l0 == 3 * lps + 2 * 5
+        with pytest.raises(dgpe.DgpeError) as e:
+            s.set_mode(True)
+        assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+        import torch
+        a = torch.zeros(32 ** 3, dtype=torch.complex128, device="cuda")
+        b = torch.zeros_like(a)
+        with pytest.raises(dgpe.DgpeError) as e:
+            dgpe.dgpe_step_adjoint(s.h, a.data_ptr(), b.data_ptr(), 0)
+        assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+    with pytest.raises(dgpe.DgpeError) as e:
+        dgpe.Solver(3, n, h, nu, 10, 5, 1e-3, True, True, split="strang")
+    assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+    q = dict(n=(64, 64), h=(0.2, 0.2), nu=(1.0, 1.0), g=10.0, gdd=5.0, dt=1e-3, imag=False,
+             split="strang")
+    with pytest.raises(dgpe.DgpeError) as e:
+        dgpe.Batch([q])
+    assert e.value.code == dgpe.DGPE_EUNSUPPORTED
