@@ -56,8 +56,10 @@ extern "C" {
 /* dgpe_params.precision */
 #define DGPE_FP64 0             /* every substep in FP64 */
 #define DGPE_FP32_BULK 1        /* FFT, exponential and Thomas arithmetic and
-                                   the state in FP32; norm/mu/energy reductions,
-                                   renormalisation and all tables built in FP64 */
+                                   the state in FP32; norm/mu/energy reductions
+                                   (the step's norm above 16-site FP32 partial
+                                   sums), renormalisation and all tables built
+                                   in FP64 */
 /* dgpe_params.kernel */
 #define DGPE_KERNEL_NONE 0
 #define DGPE_KERNEL_DIPOLAR_3D 1
@@ -91,6 +93,17 @@ extern "C" {
                                    by the exponential in real time).  Imaginary
                                    time, the reverse step and the batched form
                                    return DGPE_EUNSUPPORTED. */
+#define DGPE_FLAG_REAL_PSI 16u  /* imaginary time: hold psi as a real field
+                                   (nx reals per row; half the bytes of the
+                                   complex state).  Imaginary-time evolution
+                                   with a real potential keeps a real state
+                                   real, so the step is the complex step on
+                                   the real part.  dgpe_set_psi keeps the real
+                                   part of its input; dgpe_get_psi returns
+                                   (psi, 0).  Uses the chunk-parallel CN solve
+                                   (CN_SERIAL returns DGPE_EUNSUPPORTED), as do
+                                   real time (at create and in dgpe_set_mode)
+                                   and the batched form. */
 
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */

@@ -62,6 +62,10 @@ extern "C" int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_t *out)
   if (p->kernel < 0 || p->kernel > 3) return fail(nullptr, DGPE_EINVAL, "bad kernel");
   if ((p->flags & DGPE_FLAG_STRANG) && p->mode != DGPE_REAL)
     return fail(nullptr, DGPE_EUNSUPPORTED, "Strang splitting is defined for real time");
+  if ((p->flags & DGPE_FLAG_REAL_PSI) && p->mode != DGPE_IMAG)
+    return fail(nullptr, DGPE_EUNSUPPORTED, "a real state is an imaginary-time option");
+  if ((p->flags & DGPE_FLAG_REAL_PSI) && (p->flags & DGPE_FLAG_CN_SERIAL))
+    return fail(nullptr, DGPE_EUNSUPPORTED, "a real state uses the chunk-parallel CN solve");
   dgpe_solver *h = new (std::nothrow) dgpe_solver();
   if (!h) return fail(nullptr, DGPE_ENOMEM, "host allocation failed");
   h->stream = (cudaStream_t)cuda_stream;

@@ -277,8 +277,8 @@ extern "C" int dgpe_batch_create(const dgpe_params *ps, int count, void *cuda_st
       delete b;
       return DGPE_EUNSUPPORTED;
     }
-    if (p.flags & DGPE_FLAG_STRANG) {
-      g_batch_err = "batch problems use first-order splitting";
+    if (p.flags & (DGPE_FLAG_STRANG | DGPE_FLAG_REAL_PSI)) {
+      g_batch_err = "batch problems use first-order splitting and a complex state";
       delete b;
       return DGPE_EUNSUPPORTED;
     }

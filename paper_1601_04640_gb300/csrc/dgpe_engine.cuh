@@ -227,6 +227,10 @@ template <typename R> struct EngineT : Engine {
   cudaGraphExec_t gexec = nullptr;
   bool use_graph = true;
   bool strang = false;  // second-order splitting (real time)
+  // real state (imaginary time): psi holds nx reals per row, viewed by the
+  // strided CN passes as nx/2 complex columns (pairs of real lines)
+  bool rpsi = false;
+  Cx *ocx = nullptr;  // complex copy of a real state for the observables
 
   ~EngineT() override {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -236,7 +240,7 @@ template <typename R> struct EngineT : Engine {
                     cntab[0], cntab[1], cntab[2], prm, partial, obs_part, dip_part, obs_out,
                     dstep, counter, stage, adjG, adjT, adj_phi, adj_sig, adj_ksig, adj_part,
                     adj_acc, cntab_adj[0], cntab_adj[1], cntab_adj[2], twf[0], twf[1], twf[2],
-                    twi[0], twi[1], twi[2]};
+                    twi[0], twi[1], twi[2], ocx};
     for (void *b : bufs)
       if (b) cudaFree(b);
     for (Cx *b : ckpts) cudaFree(b);
@@ -244,6 +248,9 @@ template <typename R> struct EngineT : Engine {
   }
 
   size_t sites() const override { return nsites; }
+  // complex elements of the state buffer (a real state packs two sites in one)
+  size_t psi_elems() const { return rpsi ? nsites / 2 : nsites; }
+  int row_cx() const { return rpsi ? nx / 2 : nx; }  // complex elements per x row
 
   int launches_per_step() const override {
     int k = 1 + (dim == 3 ? 2 : 1) + (cn_serial ? 1 : 0);  // P1, CN passes
@@ -271,6 +278,8 @@ template <typename R> struct EngineT : Engine {
     nsites = (size_t)nx * ny * nz;
     imag = (p.mode == DGPE_IMAG);
     has_dip = (p.kernel != DGPE_KERNEL_NONE);
+    rpsi = (p.flags & DGPE_FLAG_REAL_PSI) != 0;
+    if (rpsi && !imag) { err = "a real state is an imaginary-time option"; return DGPE_EUNSUPPORTED; }
     px = nx / 2 + 1;
     if (sizeof(Cx) == 8) px = (px + 1) & ~1;  // 16-byte rows for FP32 complex
     ncol_spec = nx / 2 + 1;
@@ -291,8 +300,8 @@ template <typename R> struct EngineT : Engine {
       return DGPE_EUNSUPPORTED;
     }
     int rc;
-    if ((rc = dalloc(&psi, nsites))) return rc;
-    DGPE_CK(cudaMemset(psi, 0, sizeof(Cx) * nsites));
+    if ((rc = dalloc(&psi, psi_elems()))) return rc;
+    DGPE_CK(cudaMemset(psi, 0, sizeof(Cx) * psi_elems()));
     if (has_dip && (rc = dalloc(&spec, nspec))) return rc;
     if ((rc = dalloc(&prm, PRM_COUNT))) return rc;
     if ((rc = dalloc(&dstep, 1))) return rc;
@@ -422,8 +431,11 @@ template <typename R> struct EngineT : Engine {
       err = "DGPE_FLAG_CN_SERIAL and DGPE_FLAG_CN_CHUNKED are exclusive";
       return DGPE_EINVAL;
     }
-    if (sizeof(R) == 4) {
-      if (p.flags & DGPE_FLAG_CN_SERIAL) { err = "the line-serial CN solve is an FP64-form option"; return DGPE_EUNSUPPORTED; }
+    if (sizeof(R) == 4 || rpsi) {
+      if (p.flags & DGPE_FLAG_CN_SERIAL) {
+        err = rpsi ? "a real state uses the chunk-parallel CN solve" : "the line-serial CN solve is an FP64-form option";
+        return DGPE_EUNSUPPORTED;
+      }
       cn_serial = false;
     } else if (p.flags & DGPE_FLAG_CN_SERIAL) cn_serial = true;
     else if (p.flags & DGPE_FLAG_CN_CHUNKED) cn_serial = false;
@@ -445,7 +457,8 @@ template <typename R> struct EngineT : Engine {
     CnCfg &c = cn[axis];
     const int n = (axis == 1) ? ny : nz;
     c.n = n;
-    c.ncols = nx;
+    const int xw = row_cx();
+    c.ncols = xw;
     const int cl = variant_cl(var[axis]);
     const int tpl = n / cl;
     if (tpl < 1 || tpl > 32 || n % cl || !is_pow2(tpl)) { err = "line length not supported by the CN chunking"; return DGPE_EUNSUPPORTED; }
@@ -454,8 +467,8 @@ template <typename R> struct EngineT : Engine {
     c.W = std::min(W, DGPE_MAXT / tpl);  // blocks of at most DGPE_MAXT threads
     c.pitch = n + n / c.C + 1;
     c.T = c.W * tpl;
-    if (axis == 1) { c.es = nx; c.os = (long long)nx * ny; c.grid = dim3((nx + c.W - 1) / c.W, nz); }
-    else { c.es = (long long)nx * ny; c.os = nx; c.grid = dim3((nx + c.W - 1) / c.W, ny); }
+    if (axis == 1) { c.es = xw; c.os = (long long)xw * ny; c.grid = dim3((xw + c.W - 1) / c.W, nz); }
+    else { c.es = (long long)xw * ny; c.os = xw; c.grid = dim3((xw + c.W - 1) / c.W, ny); }
     c.smem = sizeof(Cx) * (size_t)c.W * c.pitch;
     return DGPE_OK;
   }
@@ -590,6 +603,8 @@ template <typename R> struct EngineT : Engine {
       int r;
       if ((r = smem_attr(k_dens_r2c_x<R, EX, 0, P2, FM>, x4_smem))) return r;
       if ((r = smem_attr(k_dens_r2c_x<R, EX, 1, P2, FM>, x4_smem))) return r;
+      if ((r = smem_attr(k_dens_r2c_x<R, EX, 2, P2, FM>, x4_smem))) return r;
+      if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 4, P2, FM1>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM1>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM1>, x_smem))) return r;
@@ -718,6 +733,7 @@ template <typename R> struct EngineT : Engine {
       constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
       constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       if (dens_in) k_dens_r2c_x<R, EX, 1, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
+      else if (rpsi && !src) k_dens_r2c_x<R, EX, 2, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
@@ -743,7 +759,9 @@ template <typename R> struct EngineT : Engine {
       constexpr bool P2 = decltype(P2c)::value;
       constexpr bool FM = P2 && (sizeof(R) == 8 || DGPE_FFT_FMA_F32);  // FMA-form twiddled stages
       constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
-      if (mode == 0) {
+      if (mode == 0 && rpsi) {
+        k_c2r_x_exp_cnx<R, R, EX, CL, 4, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
+      } else if (mode == 0) {
         if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
         else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 3) {
@@ -829,13 +847,14 @@ template <typename R> struct EngineT : Engine {
     std::vector<int> v = pass_ids();
     if (i < 0 || i >= (int)v.size()) return 0.0;
     const double S = (double)sizeof(Cx), N = (double)nsites;
+    const double SP = rpsi ? (double)sizeof(R) : S;  // bytes of psi per site
     const double sp = (double)ncol_spec * nrows, ub = sp * sizeof(R);
     switch (v[i]) {
-      case PS_DENS_R2C: return N * S + sp * S;
+      case PS_DENS_R2C: return N * SP + sp * S;
       case PS_FFT_Y: case PS_IFFT_Y: return 2.0 * sp * S;
       case PS_FFT_Z_U: case PS_FFT_Y_U: return 2.0 * sp * S + ub;
-      case PS_P1: case PS_P1_NOCN: return (has_dip ? sp * S : 0.0) + 2.0 * N * S;
-      default: return 2.0 * N * S;
+      case PS_P1: case PS_P1_NOCN: return (has_dip ? sp * S : 0.0) + 2.0 * N * SP;
+      default: return 2.0 * N * SP;
     }
   }
   // Floating-point operations of pass i per launch (an FMA counts 2), from
@@ -873,6 +892,7 @@ template <typename R> struct EngineT : Engine {
   double exp_flops_per_site() const {
     if (sizeof(R) == 8 && !imag) return (has_dip ? 8.0 : 6.0) + 19.0 + 3.0 + 6.0;
     const double th = has_dip ? 5.0 : 3.0;
+    if (rpsi) return 1 + 1 + 1 + th + 1 + 2;  // real state: V, scale, square, theta, expm1, update
     if (imag) return 1 + 2 + 3 + th + 1 + 4;
     return 1 + 2 + 3 + th + 11.0 + 8;
   }
@@ -881,6 +901,11 @@ template <typename R> struct EngineT : Engine {
   // lane scans amortised over the chunk, fix-ups)
   double cn_flops_per_site(int axis) const {
     if (cn_serial) return imag ? 16.0 : 28.0;
+    // a real state: one complex solve with real coefficients advances two sites
+    if (rpsi) return 0.5 * cn_flops_chunked(axis);
+    return cn_flops_chunked(axis);
+  }
+  double cn_flops_chunked(int axis) const {
     const int cl = (axis == 0) ? x_C : cn[axis].C;
     const int tpl = (axis == 0) ? x_TPL : cn[axis].TPL;
     const double lg = std::log2((double)std::max(tpl, 1));
@@ -893,7 +918,7 @@ template <typename R> struct EngineT : Engine {
     const double N = (double)nsites, pairs = (double)((nrows + 1) / 2);
     const double norm = (imag ? 4.0 : 0.0);  // FP64 |x|^2 accumulation of the final pass
     switch (v[i]) {
-      case PS_DENS_R2C: return 4.0 * N + pairs * fft_line_flops(plx) + pairs * (nx / 2 + 1) * 8.0;
+      case PS_DENS_R2C: return (rpsi ? 2.0 : 4.0) * N + pairs * fft_line_flops(plx) + pairs * (nx / 2 + 1) * 8.0;
       case PS_FFT_Y: case PS_IFFT_Y: return (double)ncol_spec * nz * fft_line_flops(ply);
       case PS_FFT_Z_U: return (double)ncol_spec * ny * (2.0 * fft_line_flops(plz) + 2.0 * nz);
       case PS_FFT_Y_U: return (double)ncol_spec * (2.0 * fft_line_flops(ply) + 2.0 * ny);
@@ -987,7 +1012,9 @@ template <typename R> struct EngineT : Engine {
   }
   int set_psi_device(const void *src, int fp64, cudaStream_t s) override {
     const int blocks = 152 * 8;
-    if (fp64) k_import<R, double2><<<blocks, 256, 0, s>>>(psi, (const double2 *)src, nsites);
+    if (rpsi && fp64) k_import_real<R, double2><<<blocks, 256, 0, s>>>((R *)psi, (const double2 *)src, nsites);
+    else if (rpsi) k_import_real<R, float2><<<blocks, 256, 0, s>>>((R *)psi, (const float2 *)src, nsites);
+    else if (fp64) k_import<R, double2><<<blocks, 256, 0, s>>>(psi, (const double2 *)src, nsites);
     else k_import<R, float2><<<blocks, 256, 0, s>>>(psi, (const float2 *)src, nsites);
     launched(1);
     DGPE_LCK(__func__);
@@ -997,7 +1024,9 @@ template <typename R> struct EngineT : Engine {
   }
   int get_psi_device(void *dst, int fp64, cudaStream_t s) override {
     const int blocks = 152 * 8;
-    if (fp64) k_export<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, psi, prm, nsites);
+    if (rpsi && fp64) k_export_real<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, (const R *)psi, prm, nsites);
+    else if (rpsi) k_export_real<R, float2><<<blocks, 256, 0, s>>>((float2 *)dst, (const R *)psi, prm, nsites);
+    else if (fp64) k_export<R, double2><<<blocks, 256, 0, s>>>((double2 *)dst, psi, prm, nsites);
     else k_export<R, float2><<<blocks, 256, 0, s>>>((float2 *)dst, psi, prm, nsites);
     launched(1);
     DGPE_LCK(__func__);
@@ -1006,8 +1035,18 @@ template <typename R> struct EngineT : Engine {
   int observables(dgpe_obs *o, cudaStream_t s) override {
     int rc;
     DGPE_LCK("(pending before observables)");
+    // a real state is widened to (psi, 0) first; the sums below then run
+    // unchanged on the complex copy
+    const Cx *obs_psi = psi;
+    if (rpsi) {
+      if (!ocx && (rc = dalloc(&ocx, nsites))) return rc;
+      k_widen_real<R><<<152 * 8, 256, 0, s>>>(ocx, (const R *)psi, nsites);
+      launched(1);
+      DGPE_LCK("widen");
+      obs_psi = ocx;
+    }
     if (has_dip) {
-      if ((rc = launch_forward_spectrum(s))) return rc;
+      if ((rc = launch_forward_spectrum(s, obs_psi))) return rc;
       DGPE_LCK("density/R2C");
       if (dim == 3) {
         if ((rc = launch_fft(fy, 0, s))) return rc;
@@ -1018,7 +1057,7 @@ template <typename R> struct EngineT : Engine {
       DGPE_LCK("spectral energy sum");
     }
     OArgs<R> A{};
-    A.psi = psi; A.prm = prm; A.partial = obs_part; A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
+    A.psi = obs_psi; A.prm = prm; A.partial = obs_part; A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
     A.rows_per_block = 0; A.hx = p.h[0]; A.hy = p.h[1]; A.hz = (dim == 3) ? p.h[2] : 0.0;
     A.nux = p.nu[0]; A.nuy = p.nu[1]; A.nuz = (dim == 3) ? p.nu[2] : 0.0;
     k_obs_sites<R><<<obs_blocks, 256, 0, s>>>(A);
@@ -1085,8 +1124,9 @@ template <typename R> struct EngineT : Engine {
   int set_mode(int mode, cudaStream_t s) override {
     if (mode != DGPE_IMAG && mode != DGPE_REAL) { err = "bad mode"; return DGPE_EINVAL; }
     if (strang && mode == DGPE_IMAG) { err = "Strang splitting is defined for real time"; return DGPE_EUNSUPPORTED; }
+    if (rpsi && mode == DGPE_REAL) { err = "a real state is an imaginary-time option"; return DGPE_EUNSUPPORTED; }
     // fold the lazy scale into psi, then rebuild the CN tables and the graph
-    k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, nsites);
+    k_fold_scale<R><<<152 * 8, 256, 0, s>>>(psi, prm, psi_elems());
     launched(1);
     DGPE_LCK(__func__);
     int rc = reset_scale(s);

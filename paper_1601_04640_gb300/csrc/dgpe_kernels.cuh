@@ -228,7 +228,8 @@ template <typename T> __device__ __forceinline__ const T &block_args(const T *__
   return dst;
 }
 
-// SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in.
+// SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in;
+// SRC 2: sc^2 psi^2 of a real state (A.psi holds nx reals per row).
 // FMA: twiddled stages in FMA form (tile_fft), roots from A.twf.
 template <typename R, int EPT, int SRC, bool POW2, bool FMA = false>
 __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
@@ -246,6 +247,10 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
     if (SRC == 1) {
       if (r0 < nrows) d0 = A.dens_in[(size_t)r0 * n + a];
       if (r1 < nrows) d1 = A.dens_in[(size_t)r1 * n + a];
+    } else if (SRC == 2) {
+      const R *__restrict__ pr = reinterpret_cast<const R *>(psi);
+      if (r0 < nrows) { const R v = pr[(size_t)r0 * n + a]; d0 = sc2 * (v * v); }
+      if (r1 < nrows) { const R v = pr[(size_t)r1 * n + a]; d1 = sc2 * (v * v); }
     } else {
       if (r0 < nrows) { cx<R> v = psi[(size_t)r0 * n + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
       if (r1 < nrows) { cx<R> v = psi[(size_t)r1 * n + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
@@ -289,6 +294,11 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
 // MODE 0: full substep (C2R_x, exponential, CN_x).  MODE 1: write Phi_d only.
 // MODE 2: CN_x alone (the reverse step applies it to the adjoint field).
 // MODE 3: C2R_x and the exponential, no CN (a separate CN_x pass follows).
+// MODE 4: MODE 0 for a real state in imaginary time (A.psi holds nx reals per
+//   row).  Rows 2l and 2l + 1 of the CTA share tile line l as its real and
+//   imaginary parts: the exponential scales each part by its own row's
+//   factor, and one Crank-Nicolson solve with the real coefficients of
+//   imaginary time advances both rows.
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false>
 __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -303,6 +313,10 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // global memory: its FP64 pipe, not the table loads, is the limit)
   __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
   if (!TAB && MODE != 1 && MODE != 3) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), A.nx);
+  constexpr bool RS = (MODE == 4);  // real state
+  R *const ptr = reinterpret_cast<R *>(pt);
+  // tile element of row L, column a: (line, component) for a real state
+  auto rs_at = [&](int L, int a) -> R & { return ptr[2 * ((L >> 1) * A.pitch + a + a / CL) + (L & 1)]; };
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
   const int ln = POW2 ? ilog2(n) : 0;
   const int p0 = blockIdx.x * A.LP;
@@ -320,7 +334,21 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   __shared__ __align__(16) rt4<R> s_rt[(FMA && MODE != 2) ? 512 : 1];
   const rt4<R> *rt = nullptr;
   if constexpr (FMA && MODE != 2) rt = stage_roots(s_rt, A.twi, n);
-  if (MODE != 1) {
+  if constexpr (RS) {
+    const R *__restrict__ pr = reinterpret_cast<const R *>(A.psi);
+    R buf[CL];
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      const int row = 2 * p0 + row_of(idx);
+      buf[i] = (row < nrows) ? pr[(size_t)row * n + col_of(idx)] : (R)0;
+    }
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      rs_at(row_of(idx), col_of(idx)) = buf[i];
+    }
+  } else if (MODE != 1) {
     // the CTA's rows 2 p0 .. 2 p0 + 2 LP - 1 are one contiguous block of psi:
     // every load of the tile is issued before any is used (2 LP n = CL T)
     cx<R> buf[CL];
@@ -358,6 +386,14 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // increment form.
   const R gdt_sc2 = gdt * sc * sc;
   auto apply_e = [&](int L, int a, R phi) {
+    if constexpr (RS) {
+      R &u = rs_at(L, a);
+      const R v = u * sc;
+      const R th = dts * (A.vx[a] + s_vyz[L]) + gdt * (v * v) + gdddt * phi;
+      const R f = fexpm1(-th);
+      u = v + v * f;
+      return;
+    }
     const int ia = L * P + a + a / CL;
     if (DIRECT && !imag) {
       const cx<R> u = pt[ia];
@@ -398,7 +434,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       apply_e(2 * l + 1, a, v.y);
     };
     tile_fft<R, EPT, true, false, PW, POW2, FMA>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store, rt);
-  } else if (MODE == 0 || MODE == 3) {
+  } else if (MODE == 0 || MODE == 3 || MODE == 4) {
     for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
   }
@@ -412,13 +448,25 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     }
     return;
   }
-  // Crank-Nicolson along x: TPL lanes per line
+  // Crank-Nicolson along x: TPL lanes per line (a real state: LP lines, each
+  // a pair of rows; the other half of the threads idles)
   const int l = t / A.TPL, q = t - l * A.TPL;
-  const bool active = (2 * p0 + l) < nrows;
+  const bool active = RS ? (l < A.LP && 2 * (p0 + l) < nrows) : (2 * p0 + l) < nrows;
   if constexpr (TAB) cn_line<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), active);
   else cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, active);
   __syncthreads();
+  if constexpr (RS) {
+    R *__restrict__ pr = reinterpret_cast<R *>(A.psi);
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      const int L = row_of(idx), a = col_of(idx);
+      const int row = 2 * p0 + L;
+      if (row < nrows) pr[(size_t)row * n + a] = rs_at(L, a);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
     const int idx = t + i * T;
@@ -544,13 +592,15 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   __syncthreads();
   double acc = 0.0;
   if (c0 + lc < A.ncols) {
+    R ts = (R)0;  // the thread's CL sites in R, then FP64 above the tile
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
       const int a = r0 + i * A.TPL;
       const cx<R> v = tile[lc * P + a + a / CL];
       A.psi[base + (size_t)a * es + lc] = v;
-      if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y;
+      if (A.norm) ts += v.x * v.x + v.y * v.y;
     }
+    acc = (double)ts;
   }
   if (!A.final_pass) return;
   // Last pass of the step: norm partials (imaginary time) and, in the last
@@ -645,13 +695,18 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
     __syncthreads();
     if (c0 + lc < A.ncols) {
       cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;
+      // |x|^2 of the thread's CL sites summed in R (FP32: an FP64 sum per
+      // site held the FP32 final pass at the FP64 pipe's rate, 0.21 against
+      // 0.08 ms at 256^3), then accumulated in FP64 across tiles and blocks
+      R ts = (R)0;
 #pragma unroll
       for (int i = 0; i < CL; ++i) {
         const int a = r0 + i * A.TPL;
         const cx<R> v = tb[lc * P + a + a / CL];
         dst[(size_t)a * es] = v;
-        if (A.norm) acc += (double)v.x * v.x + (double)v.y * v.y;
+        if (A.norm) ts += v.x * v.x + v.y * v.y;
       }
+      if (A.norm) acc += (double)ts;
     }
     __syncthreads();  // the buffer is refilled two iterations later
   }
@@ -1088,6 +1143,28 @@ __global__ void k_export(S *dst, const cx<R> *src, const double *prm, size_t n) 
     o.y = (decltype(o.y))(sc * (double)v.y);
     dst[i] = o;
   }
+}
+// real state (imaginary time): import the real part; export (sc psi, 0)
+template <typename R, typename S>
+__global__ void k_import_real(R *dst, const S *src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (R)src[i].x;
+}
+template <typename R, typename S>
+__global__ void k_export_real(S *dst, const R *src, const double *prm, size_t n) {
+  const double sc = prm[PRM_SC];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    S o;
+    o.x = (decltype(o.x))(sc * (double)src[i]);
+    o.y = (decltype(o.y))0;
+    dst[i] = o;
+  }
+}
+// real state -> complex (v, 0), unscaled (the observables' input)
+template <typename R>
+__global__ void k_widen_real(cx<R> *dst, const R *src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = mk<R>(src[i], (R)0);
 }
 template <typename R>
 __global__ void k_fold_scale(cx<R> *psi, double *prm, size_t n) {

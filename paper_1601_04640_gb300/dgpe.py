@@ -37,6 +37,7 @@ DGPE_FLAG_NO_GRAPH = 1
 DGPE_FLAG_CN_SERIAL = 2
 DGPE_FLAG_CN_CHUNKED = 4
 DGPE_FLAG_STRANG = 8
+DGPE_FLAG_REAL_PSI = 16
 
 EXPORTS = [
     "dgpe_create", "dgpe_destroy", "dgpe_set_psi", "dgpe_get_psi", "dgpe_set_psi_device",
@@ -132,10 +133,10 @@ def _check(rc, h=None):
 
 
 def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                kernel=None, qd=0.5, graph=True, cn=None, plane=None, split="lie"):
+                kernel=None, qd=0.5, graph=True, cn=None, plane=None, split="lie", real_psi=False):
     """cn: None (automatic), "serial" or "chunked" (FP64 Crank-Nicolson form).
     split: "lie" (the paper's first-order step) or "strang" (second order,
-    real time).
+    real time).  real_psi: hold the state as a real field (imaginary time).
     plane (2D): "xy" or "xz"; default XZ for the XZ kernel, else XY.  For XZ the
     second axis is z: n, h, nu = (nx, nz), (hx, hz), (nu_x, nu_z)."""
     p = dgpe_params()
@@ -166,6 +167,8 @@ def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
         p.flags |= DGPE_FLAG_STRANG
     elif split != "lie":
         raise ValueError("split must be 'lie' or 'strang'")
+    if real_psi:
+        p.flags |= DGPE_FLAG_REAL_PSI
     return p
 
 
@@ -285,12 +288,13 @@ class Solver:
     """One condensate on the GPU: create, set/get psi, step, observe."""
 
     def __init__(self, dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                 kernel=None, qd=0.5, graph=True, stream: int = 0, cn=None, split="lie"):
+                 kernel=None, qd=0.5, graph=True, stream: int = 0, cn=None, split="lie",
+                 real_psi=False):
         self.dim = dim
         self.n = tuple(n)
         self.shape = (n[2], n[1], n[0]) if dim == 3 else (n[1], n[0])
         self.params = make_params(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel, qd, graph, cn,
-                                  split=split)
+                                  split=split, real_psi=real_psi)
         self.h = dgpe_create(self.params, stream)
 
     def close(self):
@@ -408,7 +412,8 @@ class Batch:
         self.shapes = []
         for i, q in enumerate(problems):
             arr[i] = make_params(2, q["n"], q["h"], q["nu"], q["g"], q["gdd"], q["dt"], q["imag"], False,
-                                 DGPE_KERNEL_QUASI2D_XY, q.get("qd", 0.5), split=q.get("split", "lie"))
+                                 DGPE_KERNEL_QUASI2D_XY, q.get("qd", 0.5), split=q.get("split", "lie"),
+                                 real_psi=q.get("real_psi", False))
             self.shapes.append((q["n"][1], q["n"][0]))
         self.h = C.c_void_p()
         rc = lib.dgpe_batch_create(arr, len(problems), C.c_void_p(stream), C.byref(self.h))

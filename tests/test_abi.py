@@ -85,6 +85,12 @@ def test_argument_errors_without_device(lib):
     with pytest.raises(dgpe.DgpeError) as e:
         dgpe.dgpe_create(p)
     assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+    # a real state is an imaginary-time option on the chunk-parallel CN solve
+    for kw in (dict(imag=False), dict(imag=True, cn="serial")):
+        p = dgpe.make_params(3, (32, 32, 32), (0.25,) * 3, (1, 1, 2), real_psi=True, **kw)
+        with pytest.raises(dgpe.DgpeError) as e:
+            dgpe.dgpe_create(p)
+        assert e.value.code == dgpe.DGPE_EUNSUPPORTED
 
 
 def test_product_path_does_not_reference_the_oracle():

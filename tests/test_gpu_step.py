@@ -464,3 +464,77 @@ def test_strang_launches_and_refusals():
     with pytest.raises(dgpe.DgpeError) as e:
         dgpe.Batch([q])
     assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+
+
+# (dim, n, h, nu, fp64, kernel)
+REAL_STATE_CASES = [
+    (3, (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0), True, None),
+    (3, (32, 32, 32), (0.25,) * 3, (1.0, 1.0, 2.0), False, None),
+    (3, (64, 32, 128), (0.2, 0.3, 0.1), (1.0, 1.3, 0.8), True, None),
+    (3, (96, 160, 48), (0.2, 0.15, 0.3), (1.0, 1.2, 1.5), False, None),
+    (3, (160, 48, 40), (0.15, 0.3, 0.3), (1.0, 1.4, 1.2), True, "none"),
+    (2, (64, 32), (0.2, 0.3), (1.0, 1.5), True, None),
+    (2, (96, 64), (0.2, 0.25), (1.0, 1.5), False, "xz"),
+    (2, (384, 96), (0.05, 0.2), (1.0, 1.5), False, None),
+]
+
+
+@pytest.mark.parametrize("case", range(len(REAL_STATE_CASES)))
+def test_step_parity_real_state(case):
+    """Real state in imaginary time (nx reals per row; rows paired into the
+    complex lines of the x-line pass, columns paired by the strided CN passes)
+    against the oracle's complex step on the same real input, with a
+    modulated trap; the state read back is real; mu and E of the result."""
+    dim, n, h, nu, fp64, kernel = REAL_STATE_CASES[case]
+    g, gdd, dt, cm = 50.0, (0.0 if kernel == "none" else 15.0), 2e-3, [0.3]
+    op, kc, psi0 = make_case(dim, n, h, nu, g, gdd, dt, True, kernel=kernel, noise=0.05)
+    psi0 = psi0.real.astype(np.complex128)
+    op.cm = cm
+    with dgpe.Solver(dim, n, h, nu, g, gdd, dt, True, fp64, kernel=kc, real_psi=True) as s:
+        s.set_psi(psi0)
+        s.set_trap_modulation(cm)
+        s.step(4)
+        s.step(6)
+        psi = s.get_psi()
+        o = s.observables()
+        assert s.time() == 10
+    ref = oracle.step(op, psi0, 0, 10)
+    r = oracle.observables(op, ref, 10)
+    e = rel_l2(psi, ref)
+    print("rel L2", e, "mu", o["mu"], r["mu"])
+    assert np.all(psi.imag == 0.0)
+    assert e < TOL_PSI[fp64]
+    for k in ("norm", "mu", "energy"):
+        assert abs(o[k] - r[k]) <= TOL_MU[fp64] * max(1.0, abs(r[k])), (k, o[k], r[k])
+
+
+def test_real_state_bytes_potential_and_refusals():
+    n, h, nu = (64, 32, 48), (0.2, 0.3, 0.25), (1.0, 1.3, 0.9)
+    psi0 = synth.gaussian_state(n, h, nu, 0.05, 21).real.astype(np.complex128)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=30, gdd=12, dt=1e-3, imag=True, kernel="dipolar3d")
+    ref = oracle.dipolar_potential(op, np.abs(psi0) ** 2)
+    lib = dgpe.load()
+    with dgpe.Solver(3, n, h, nu, 30, 12, 1e-3, True, True, cn="chunked") as c, \
+            dgpe.Solver(3, n, h, nu, 30, 12, 1e-3, True, True, real_psi=True) as s:
+        s.set_psi(psi0)
+        phi = s.dipolar_potential()
+        assert np.max(np.abs(phi - ref)) / np.max(np.abs(ref)) < 1e-12
+        lps = dgpe.dgpe_launches_per_step(s.h)
+        assert lps == dgpe.dgpe_launches_per_step(c.h)
+        names = [lib.dgpe_pass_name(s.h, i).decode() for i in range(lps)]
+        bs = [lib.dgpe_pass_bytes(s.h, i) for i in range(lps)]
+        bc = [lib.dgpe_pass_bytes(c.h, i) for i in range(lps)]
+        sites = 64 * 32 * 48
+        for name, a, b in zip(names, bs, bc):
+            if name in ("cn_y", "cn_z"):
+                assert a == 2 * 8 * sites and b == 2 * 16 * sites
+            if name == "c2r_x_exp_cn_x":
+                assert b - a == 2 * 8 * sites
+        with pytest.raises(dgpe.DgpeError) as e:
+            s.set_mode(False)
+        assert e.value.code == dgpe.DGPE_EUNSUPPORTED
+    q = dict(n=(64, 64), h=(0.2, 0.2), nu=(1.0, 1.0), g=10.0, gdd=5.0, dt=1e-3, imag=True,
+             real_psi=True)
+    with pytest.raises(dgpe.DgpeError) as e:
+        dgpe.Batch([q])
+    assert e.value.code == dgpe.DGPE_EUNSUPPORTED
