@@ -154,7 +154,7 @@ int launch_class(dgpe_batch *b, Cls &c, cudaStream_t s) {
     } else {
       k_c2r_x_exp_cnx_batch<float, Cx, EX, CL, P2><<<xg, c.xT, c.xs, s>>>(c.dX);
       if (cudaPeekAtLastError() != cudaSuccess) return 3;
-      k_cn_strided_batch<float, Cx, CL><<<c.cgrid, c.cT, c.cs, s>>>(c.dC);
+      k_cn_strided_batch<float, Cx, CL, false><<<c.cgrid, c.cT, c.cs, s>>>(c.dC);  // real time: no norm
     }
     if (cudaPeekAtLastError() != cudaSuccess) return 4;
     return 0;
@@ -179,7 +179,7 @@ int set_attrs(dgpe_batch *b, const Cls &c) {
     if (e == cudaSuccess) e = attr(k_c2r_x_exp_cnx_batch<float, float, EX, CL, P2>, xs);
     if (e == cudaSuccess) e = attr(k_c2r_x_exp_cnx_batch<float, Cx, EX, CL, P2>, xs);
     if (e == cudaSuccess) e = attr(k_cn_strided_batch<float, float, CL>, c.cs);
-    if (e == cudaSuccess) e = attr(k_cn_strided_batch<float, Cx, CL>, c.cs);
+    if (e == cudaSuccess) e = attr(k_cn_strided_batch<float, Cx, CL, false>, c.cs);
     with_svar<Eng::EPT_S>(c.var, [&](auto EPc, auto SP2c) -> int {
       constexpr int EP = decltype(EPc)::value;
       constexpr bool SP2 = decltype(SP2c)::value;

@@ -636,13 +636,15 @@ template <typename R> struct EngineT : Engine {
         if ((r = smem_attr(k_cn_strided<R, Cx, CL>, one))) return r;
         if ((r = smem_attr(k_cn_strided_pipe<R, R, CL>, two))) return r;
         if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL>, two))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, R, CL, false>, two))) return r;
+        if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL, false>, two))) return r;
         // persistent grid: as many CTAs as fit on the device, at most one per
         // tile, each double-buffered (the next tile is prefetched)
         const int ntiles = (int)(cn[a].grid.x * cn[a].grid.y);
         int occ = 0;
         DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, R, CL>, cn[a].T, two));
         cn[a].pgrid[0] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
-        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, Cx, CL>, cn[a].T, two));
+        DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cn_strided_pipe<R, Cx, CL, false>, cn[a].T, two));
         cn[a].pgrid[1] = std::max(1, std::min(ntiles, nsm * std::max(occ, 1)));
         return DGPE_OK;
       });
@@ -699,8 +701,10 @@ template <typename R> struct EngineT : Engine {
     const int ncb = (int)c.grid.x, ntiles = (int)(c.grid.x * c.grid.y);
     with_cl(var[axis], [&](auto CLc) -> int {
       constexpr int CL = decltype(CLc)::value;
-      if (imag) k_cn_strided_pipe<R, R, CL><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
-      else k_cn_strided_pipe<R, Cx, CL><<<c.pgrid[1], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+      // the norm's code only in the pass that takes the norm
+      if (imag && A.norm) k_cn_strided_pipe<R, R, CL, true><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+      else if (imag) k_cn_strided_pipe<R, R, CL, false><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+      else k_cn_strided_pipe<R, Cx, CL, false><<<c.pgrid[1], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
       return DGPE_OK;
     });
     launched(1);

@@ -102,7 +102,7 @@ template <> __device__ __forceinline__ float2 make_kt<float2>(double tau) { retu
 // arguments use the half-angle identities cos x - 1 = -2 sin^2(x/2) and
 // sin x = 2 sin(x/2) cos(x/2) with the library sincos.
 template <typename R> __device__ __forceinline__ void sin_cosm1(R x, R *sn, R *cm1) {
-  if (fabs((double)x) <= 0.125) {
+  if (fabs(x) <= (R)0.125) {  // compared in R: an FP64 compare per site is FP64-pipe work in the FP32 form
     const R x2 = x * x;
     R ps, pc;
     if (sizeof(R) == 8) {
@@ -305,7 +305,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
   cx<R> *zt = pt + 2 * A.LP * A.pitch;           // Z tile: LP lines, pitch pitchz
   constexpr int PW = Pad<R>::W;
-  __shared__ double s_dts;
+  __shared__ R s_k[4];  // dt s(t) f, g dt f, g_dd dt f, sc (thread 0, from FP64)
   __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
   constexpr bool TAB = (sizeof(R) == 8);
   __shared__ R s_dvx[TAB ? 512 : 1];  // FP64 real time: dt s(t) V_x
@@ -366,12 +366,14 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
       pt[L * P + a + a / CL] = buf[i];
     }
   }
-  if (t == 0) s_dts = trap_dts(A.prm, *A.step) * A.dtf;
+  if (t == 0) {
+    s_k[0] = (R)(trap_dts(A.prm, *A.step) * A.dtf);
+    s_k[1] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_G]);
+    s_k[2] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_GDD]);
+    s_k[3] = (R)A.prm[PRM_SC];
+  }
   __syncthreads();
-  const R dts = (R)s_dts;
-  const R gdt = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_G]);
-  const R gdddt = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_GDD]);
-  const R sc = (R)A.prm[PRM_SC];
+  const R dts = s_k[0], gdt = s_k[1], gdddt = s_k[2], sc = s_k[3];
   const int imag = A.imag;
   constexpr bool DIRECT = (sizeof(R) == 8);  // FP64: the direct (scaled) phase factor in real time
   if (DIRECT && !imag && MODE != 1 && MODE != 2) {
@@ -552,7 +554,9 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_st
 }
 
 // ------------------------------------------------------- P2 / P3 (strided)
-template <typename R, typename Coef, int CL>
+// NORM false: a pass without the norm (no |x|^2 code at all); true: the
+// runtime flag A.norm decides.
+template <typename R, typename Coef, int CL, bool NORM = true>
 __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *tile = reinterpret_cast<cx<R> *>(smraw);  // [W][pitch]
@@ -598,7 +602,7 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
       const int a = r0 + i * A.TPL;
       const cx<R> v = tile[lc * P + a + a / CL];
       A.psi[base + (size_t)a * es + lc] = v;
-      if (A.norm) ts += v.x * v.x + v.y * v.y;
+      if (NORM && A.norm) ts += v.x * v.x + v.y * v.y;
     }
     acc = (double)ts;
   }
@@ -635,22 +639,22 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
     *A.counter = 0u;
   }
 }
-template <typename R, typename Coef, int CL>
+template <typename R, typename Coef, int CL, bool NORM = true>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided(const __grid_constant__ CArgs<R> A) {
-  cn_strided_body<R, Coef, CL>(A);
+  cn_strided_body<R, Coef, CL, NORM>(A);
 }
-template <typename R, typename Coef, int CL>
+template <typename R, typename Coef, int CL, bool NORM = true>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
   __shared__ CArgs<R> sA;
   const CArgs<R> &A = block_args(args, sA);
-  cn_strided_body<R, Coef, CL>(A);
+  cn_strided_body<R, Coef, CL, NORM>(A);
 }
 
 // Persistent, double-buffered CN pass: each CTA walks tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the copies of the next tile into
 // the other shared buffer are in flight while the current tile is solved.
 // Tile id -> (column block id % nx_blocks, outer index id / nx_blocks).
-template <typename R, typename Coef, int CL>
+template <typename R, typename Coef, int CL, bool NORM = true>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(const __grid_constant__ CArgs<R> A, int ncb, int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
@@ -704,16 +708,16 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
         const int a = r0 + i * A.TPL;
         const cx<R> v = tb[lc * P + a + a / CL];
         dst[(size_t)a * es] = v;
-        if (A.norm) ts += v.x * v.x + v.y * v.y;
+        if (NORM && A.norm) ts += v.x * v.x + v.y * v.y;
       }
-      if (A.norm) acc += (double)ts;
+      if (NORM && A.norm) acc += (double)ts;
     }
     __syncthreads();  // the buffer is refilled two iterations later
   }
   cp_async_wait<0>();
   if (!A.final_pass) return;
   const unsigned nblk = gridDim.x;
-  if (A.norm) {
+  if (NORM && A.norm) {
     double sblk = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[blockIdx.x] = sblk;
   }
@@ -725,7 +729,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  if (A.norm) {
+  if (NORM && A.norm) {
     double sum = 0.0;
     for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) sum += __ldcg(A.partial + i);
     sum = block_sum(sum, red);
