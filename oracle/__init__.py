@@ -108,6 +108,7 @@ def load():
         lib.or_nonlinear_frac.argtypes = [P, cp, C.c_double, C.c_double]
         lib.or_thomas.argtypes = [cp, cp, cp, cp, cp, C.c_int]
         lib.or_cn_axis.argtypes = [P, cp, C.c_int]
+        lib.or_cn_axis_adjoint.argtypes = [P, cp, C.c_int]
         lib.or_normalize.argtypes = [P, cp]
         lib.or_step.argtypes = [P, cp, C.c_long]
         lib.or_run.argtypes = [P, cp, C.c_long, C.c_long]
@@ -221,6 +222,13 @@ def thomas(a, b, c, d):
 def cn_axis(p: Params, psi, axis):
     psi = _c128(psi)
     load().or_cn_axis(C.byref(p._c()), psi, int(axis))
+    return psi
+
+
+def cn_axis_adjoint(p: Params, psi, axis):
+    """C_a^dagger psi (the conjugate transpose of the CN substep along axis)."""
+    psi = _c128(psi)
+    load().or_cn_axis_adjoint(C.byref(p._c()), psi, int(axis))
     return psi
 
 

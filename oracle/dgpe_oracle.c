@@ -433,6 +433,11 @@ void or_cn_axis(const or_params *p, double complex *psi, int axis) {
   cn_axis_sign(p, psi, axis, 0);
 }
 
+/* The adjoint C_a^dagger of the Crank-Nicolson substep along `axis`. */
+void or_cn_axis_adjoint(const or_params *p, double complex *psi, int axis) {
+  cn_axis_sign(p, psi, axis, 1);
+}
+
 /* psi <- psi / sqrt(h^d sum |psi|^2) */
 void or_normalize(const or_params *p, double complex *psi) {
   long N = nsites(p);

@@ -76,6 +76,7 @@ void or_thomas(const double complex *a, const double complex *b,
                const double complex *c, const double complex *d,
                double complex *x, int n);
 void or_cn_axis(const or_params *p, double complex *psi, int axis);
+void or_cn_axis_adjoint(const or_params *p, double complex *psi, int axis);
 void or_normalize(const or_params *p, double complex *psi);
 int or_step(const or_params *p, double complex *psi, long step);
 int or_run(const or_params *p, double complex *psi, long step0, long nsteps);
