@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the cuFFT comparison step")
     ap.add_argument("--no-strang", action="store_true", help="skip the second-order splitting leg")
     ap.add_argument("--no-real-psi", action="store_true", help="skip the real-state leg (imaginary time)")
+    ap.add_argument("--no-launch-cmp", action="store_true",
+                    help="skip the graph-replay vs direct-launch comparison (states that fit in L2)")
     ap.add_argument("--cn", default="auto", choices=["auto", "serial", "chunked"],
                     help="Crank-Nicolson solve form of the FP64 form (auto: the library's default "
                          "for the grid size); the FP32 form always uses the chunk-parallel solve")
@@ -381,6 +383,44 @@ def main():
         S.close()
         forms[name] = f
 
+    # launch-bound sizes (the state fits in L2): steps/s with the step replayed
+    # as one CUDA graph against its kernels launched one by one, back to back
+    # and with an L2 flush before every step
+    launch_cmp = None
+    if flush is not None and not args.no_launch_cmp:
+        launch_cmp = {}
+        for fp64 in order:
+            name = "fp64" if fp64 else "fp32_bulk"
+            row = {}
+            for graph in (True, False):
+                key = "graph" if graph else "direct"
+                with dgpe.Solver(dim, n, wl["h"], wl["nu"], wl["g"], wl["gdd"], wl["dt"], imag, fp64, kernel=kcode,
+                                 qd=qd, stream=stream.cuda_stream, graph=graph) as S4:
+                    S4.set_psi(psi0)
+                    S4.step(args.warmup)
+                    barrier()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    S4.step(args.steps)
+                    e1.record(stream)
+                    barrier()
+                    b2b = shard.max_over_ranks(e0.elapsed_time(e1)) / args.steps
+                    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(args.steps)]
+                    with torch.cuda.stream(stream):
+                        for a0, a1 in evs:
+                            flush.add_(1.0)
+                            a0.record(stream)
+                            S4.step(1)
+                            a1.record(stream)
+                    barrier()
+                    fl = shard.max_over_ranks(sum(a0.elapsed_time(a1) for a0, a1 in evs)) / args.steps
+                row[key] = {"ms_per_step_back_to_back": b2b, "steps_per_s_back_to_back": 1e3 / b2b,
+                            "ms_per_step_l2_flushed": fl, "steps_per_s_l2_flushed": 1e3 / fl}
+            row["graph_speedup_back_to_back"] = row["direct"]["ms_per_step_back_to_back"] / row["graph"]["ms_per_step_back_to_back"]
+            launch_cmp[name] = row
+
     # second-order (Strang) splitting on the same workload and state: one
     # dgpe_step(K) call runs K first-order steps between two exponential
     # passes over -dt/2 and +dt/2
@@ -518,6 +558,7 @@ def main():
         "fp32_bulk": b,
         "cufft_plain_step": plain,
         "strang_split": strang,
+        "graph_vs_direct": launch_cmp,
         "real_state": real_state,
         "speedup_fp32_bulk_vs_fp64": (b["value"] / a["value"]) if b else None,
         "source_hash": source_hash(),
