@@ -527,6 +527,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         import oracle.build
         oracle.build.build()
+        run_oracle_sample(wl, seconds=0.0, max_steps=1)  # untimed warm-up step (thread pool, first touch)
         cpu, _, _ = run_oracle_sample(wl)
         # the paper's baseline is one CPU core: the same oracle on one thread
         import oracle
