@@ -48,7 +48,10 @@ extern "C" {
 #define DGPE_ENOMEM (-3)        /* device allocation failed */
 #define DGPE_ECUDA (-4)         /* a CUDA call failed */
 #define DGPE_ENONFINITE (-5)    /* NaN or Inf found in the state */
-#define DGPE_ETIMEOUT (-6)      /* a bounded device-side wait ran out */
+#define DGPE_ETIMEOUT (-6)      /* a bounded device-side wait ran out (reserved:
+                                   no kernel of this version waits on another
+                                   block or device; the step's final pass takes
+                                   a last-block ticket instead) */
 
 /* dgpe_params.mode */
 #define DGPE_IMAG 0             /* imaginary time: stationary states */
