@@ -218,6 +218,22 @@ def test_real3d_256_short_parity():
         assert e < TOL_PSI[fp64]
 
 
+def test_large_512x512x256_short_parity():
+    """The 512 x 512 x 256 pancake workload (h = 0.08, nu = (1, 1, 3), g = 500,
+    g_dd = 200, dt = 2e-4) at full size from its seed-2016 Gaussian: two
+    steps against the oracle, both forms."""
+    n, h, nu = (512, 512, 256), (0.08,) * 3, (1.0, 1.0, 3.0)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=500, gdd=200, dt=2e-4, imag=False, kernel="dipolar3d")
+    psi0 = synth.gaussian_state(n, h, nu, 0.01, 2016)
+    ref = oracle.step(op, psi0, 0, 2)
+    for fp64 in (True, False):
+        psi, o = gpu_run(3, n, h, nu, 500, 200, 2e-4, False, fp64, None, psi0, 2)
+        e = rel_l2(psi, ref)
+        print("fp64" if fp64 else "fp32", "rel L2", e)
+        assert e < TOL_PSI[fp64]
+        del psi
+
+
 @pytest.mark.parametrize("fp64", [True, False])
 def test_real_time_norm_conserved(fp64):
     n, h, nu = (64, 64, 64), (0.2,) * 3, (1.0, 1.0, 0.5)
