@@ -159,6 +159,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def workload_config(wl, form, world=1):
+    """The `config` dict of a 3D/2D step workload, the same on both arms."""
+    n = wl["n"]
+    sites = int(np.prod(n))
+    fits = 16 * sites < (256 << 20)
+    return {"workload": wl["desc"], "grid": list(n), "sites": sites, "form": form,
+            "l2": ("inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
+                16 * sites >> 20, 8 * sites >> 20)) if not fits else
+                  "L2 flushed before every timed step (256 MB write outside the step's events); "
+                  "the state (%.1f MB FP64) fits in L2" % (16 * sites / 2 ** 20),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "prep_imag_steps": wl["prep_steps"] if wl.get("g_prep") is not None else 0}
+
+
 def run_oracle_sample(wl, seconds=12.0, max_steps=3):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -232,7 +246,9 @@ def main():
         line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": "site-updates/s",
                 "n_gpus": 0, "steps": steps, "warmup": W, "ms_per_step": 1e3 * dt / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": wl["desc"], "grid": list(n)},
+                "data": "synthetic", "config": workload_config(wl, "fp64" if args.forms != "fp32" else "fp32_bulk"),
+                "start": "seeded Gaussian of the workload (the oracle's cost per step does not depend on the "
+                         "state; the GPU arm starts from its prepared state)",
                 "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
                 "e2e": {"value": cb["value"], "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -545,15 +561,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": a["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": a["dtype"],
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "grid": list(n), "sites": sites,
-                   "form": "fp64" if "fp64" in forms else "fp32_bulk",
-                   "l2": ("inputs larger than L2: psi %d MB (FP64) / %d MB (FP32) vs 129 MB L2" % (
-                       16 * sites >> 20, 8 * sites >> 20)) if flush is None else
-                         "L2 flushed before every timed step (256 MB write outside the step's events); "
-                         "the state (%.1f MB FP64) fits in L2" % (16 * sites / 2 ** 20),
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
-                                                      "mu": prep["mu"]}},
+        "config": workload_config(wl, "fp64" if "fp64" in forms else "fp32_bulk", world),
+        "prep": None if prep is None else {"imag_steps": wl["prep_steps"], "g": wl["g_prep"],
+                                           "mu": prep["mu"]},
         "roofline": a["roofline"], "roofline_hbm": a["roofline_hbm"], "step_hbm": a["step_hbm"],
         "step_flops": a["step_flops"], "passes": a["passes"],
         "cpu_baseline": cpu, "e2e": a.get("e2e"),

@@ -44,14 +44,19 @@ extern "C" {
 /* status codes */
 #define DGPE_OK 0
 #define DGPE_EINVAL (-1)        /* bad argument or parameter */
-#define DGPE_EUNSUPPORTED (-2)  /* valid but not supported (grid size, XZ plane) */
+#define DGPE_EUNSUPPORTED (-2)  /* valid but not supported: a grid length
+                                   outside the supported set, or a flag that
+                                   the mode or form does not take */
 #define DGPE_ENOMEM (-3)        /* device allocation failed */
 #define DGPE_ECUDA (-4)         /* a CUDA call failed */
 #define DGPE_ENONFINITE (-5)    /* NaN or Inf found in the state */
-#define DGPE_ETIMEOUT (-6)      /* a bounded device-side wait ran out (reserved:
-                                   no kernel of this version waits on another
-                                   block or device; the step's final pass takes
-                                   a last-block ticket instead) */
+#define DGPE_ETIMEOUT (-6)      /* a bounded device-side wait ran out: a kernel
+                                   gave up waiting for its own asynchronous
+                                   copies (or, in the batched form, for another
+                                   block's pass) and returned; the state is then
+                                   incomplete.  Reported by dgpe_observables
+                                   and dgpe_sync (dgpe_batch_step for the
+                                   batched form) */
 
 /* dgpe_params.mode */
 #define DGPE_IMAG 0             /* imaginary time: stationary states */
@@ -108,12 +113,18 @@ extern "C" {
                                    real time (at create and in dgpe_set_mode)
                                    and the batched form. */
 
+#define DGPE_FLAG_P1_ONESHOT 32u /* FP32 bulk: run the x-line pass (C2R, exponential,
+                                   CN_x) as one CTA per tile instead of the
+                                   default persistent CTAs fed by bulk
+                                   asynchronous copies (same arithmetic) */
+
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */
   int plane;        /* DGPE_PLANE_* (2D) */
-  int n[3];         /* nx, ny, nz (nz ignored in 2D); each a power of two
-                       between 32 and 512 (other 2^a 3^b 5^c lengths return
-                       DGPE_EUNSUPPORTED) */
+  int n[3];         /* nx, ny, nz (nz ignored in 2D); each 2^k, 3 2^k or
+                       5 2^k between 32 and 512 (e.g. 64, 96, 160, 384);
+                       any other length (240 = 16 15 included) returns
+                       DGPE_EUNSUPPORTED */
   double h[3];      /* spacings hx, hy, hz > 0 */
   double nu[3];     /* trap frequencies nu_x, nu_y, nu_z >= 0 */
   double g;         /* contact strength */
@@ -121,7 +132,8 @@ typedef struct dgpe_params {
   double dt;        /* time step > 0 */
   int mode;         /* DGPE_IMAG or DGPE_REAL */
   int precision;    /* DGPE_FP64 or DGPE_FP32_BULK */
-  int kernel;       /* DGPE_KERNEL_* (DIPOLAR_3D needs dim 3, QUASI2D_XY dim 2) */
+  int kernel;       /* DGPE_KERNEL_* (DIPOLAR_3D needs dim 3, QUASI2D_XY dim 2
+                       and the XY plane, QUASI2D_XZ dim 2 and the XZ plane) */
   double qd;        /* quasi-2D width d > 0 of the transverse profile (z for
                        QUASI2D_XY, y for QUASI2D_XZ) */
   unsigned flags;   /* DGPE_FLAG_* */
@@ -271,8 +283,9 @@ const char *dgpe_batch_last_error(dgpe_batch_t b);
  *        else complex64, layout [z][y][x] / [y][x];
  *   phi: device buffer of n_sites reals (double when fp64 != 0, else float);
  *   dim, n, h, kernel, qd: as in dgpe_params (kernel DIPOLAR_3D with dim 3 or
- *        QUASI2D_XY with dim 2); each n a power of two in [32, 512] and at
- *        most 262144 sites in total, else DGPE_EUNSUPPORTED;
+ *        QUASI2D_XY with dim 2; QUASI2D_XZ returns DGPE_EUNSUPPORTED); each
+ *        n a power of two in [32, 512] and at most 262144 sites in total,
+ *        else DGPE_EUNSUPPORTED;
  *   cuda_stream: cudaStream_t (NULL = legacy default stream); asynchronous.
  * All scratch (half spectrum, U(k)/N, FFT roots) lives in one 4 MiB static
  * device array that every GPU loading this library keeps until exit.  The
@@ -280,6 +293,9 @@ const char *dgpe_batch_last_error(dgpe_batch_t b);
  * current), so make it before any stream capture.  Every call reuses the same
  * array and re-initialises what it reads first; calls that overlap on the GPU
  * (other streams, other threads) race on it.  No allocation of any kind.
+ * The array's address is looked up once per device and kept: do not call
+ * this entry point again after cudaDeviceReset in the same process.
+ * Devices 0..63 only.
  * Errors: DGPE_EINVAL / DGPE_EUNSUPPORTED / DGPE_ECUDA, text in
  * dgpe_noalloc_last_error(). */
 int dgpe_dipolar_potential_noalloc(const void *psi, void *phi, int fp64, int dim,

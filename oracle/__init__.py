@@ -97,6 +97,8 @@ def load():
         lib.or_kernel_q2d.argtypes = [dp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double]
         lib.or_q2d_value.argtypes = [C.c_double, C.c_double]
         lib.or_q2d_value.restype = C.c_double
+        lib.or_erfcx.argtypes = [C.c_double]
+        lib.or_erfcx.restype = C.c_double
         lib.or_kernel_q2dxz.argtypes = [dp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double]
         lib.or_q2dxz_value.argtypes = [C.c_double, C.c_double, C.c_double]
         lib.or_q2dxz_value.restype = C.c_double
@@ -172,6 +174,11 @@ def kernel_q2d(n, h, d):
 
 def q2d_value(k, d):
     return load().or_q2d_value(float(k), float(d))
+
+
+def erfcx(u):
+    """exp(u^2) erfc(u), u >= 0, as the quasi-2D kernels evaluate it."""
+    return load().or_erfcx(float(u))
 
 
 def kernel_q2dxz(n, h, d):

@@ -229,6 +229,8 @@ static double erfcx_pos(double u) {
   return sum / (u * sqrt(M_PI));
 }
 
+double or_erfcx(double u) { return erfcx_pos(u); }
+
 /* Quasi-2D XY kernel: the 3D kernel averaged over the z-profile
  * |phi(z)|^2 = exp(-z^2/d^2) / (sqrt(pi) d):
  *   U2(k) = (4 pi/3) / (sqrt(2 pi) d) * [2 - 3 sqrt(pi/2) q erfcx(q / sqrt 2)],

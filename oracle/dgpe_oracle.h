@@ -58,6 +58,8 @@ int or_fftn(double complex *a, const int *dims, int ndim, int sign);
 void or_kernel_3d(double *U, const int n[3], const double h[3]);
 void or_kernel_q2d(double *U, const int n[3], const double h[3], double d);
 double or_q2d_value(double krho, double d);
+/* erfcx(u) = exp(u^2) erfc(u) for u >= 0, as the quasi-2D kernels use it. */
+double or_erfcx(double u);
 /* Quasi-2D XZ kernel on the (nz, nx) grid (n[1], h[1] hold the z axis). */
 void or_kernel_q2dxz(double *U, const int n[3], const double h[3], double d);
 double or_q2dxz_value(double kx, double kz, double d);

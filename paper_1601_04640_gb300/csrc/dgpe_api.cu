@@ -171,7 +171,7 @@ extern "C" int dgpe_sync(dgpe_t h) {
   CHECK_H(h);
   cudaError_t e = h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(h, DGPE_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
-  return DGPE_OK;
+  return from_engine(h, h->eng->wait_status(h->stream));
 }
 
 extern "C" int dgpe_launches_per_step(dgpe_t h) {

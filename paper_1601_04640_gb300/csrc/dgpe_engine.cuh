@@ -46,6 +46,8 @@ struct Engine {
   virtual double pass_flops(int i) const = 0;
   virtual long long kernel_launches() const = 0;
   virtual size_t sites() const = 0;
+  // DGPE_ETIMEOUT if a kernel's bounded wait ran out since the last set_psi
+  virtual int wait_status(cudaStream_t s) = 0;
   std::string err;
 };
 
@@ -198,6 +200,11 @@ template <typename R> struct EngineT : Engine {
   // pass configurations
   int x_LP = 0, x_T = 0, x_TPL = 0, x_C = 0, x_pitchz = 0, x_pitch = 0, x_grid = 0;
   size_t x_smem = 0, x4_smem = 0;  // the C2R/exp/CN pass; the density pass (Z tile only)
+  // FP32 bulk, complex state, power-of-two nx: the pipelined x-line pass
+  // (k_p1_pipe, persistent CTAs fed by bulk copies); grid and shared memory
+  bool p1_pipe = false;
+  int p1_grid[2] = {0, 0};  // real, complex CN coefficients
+  size_t p1_smem[2] = {0, 0};
   struct CnCfg {
     int n, ncols, W, TPL, C, pitch, T;
     long long es, os;
@@ -610,6 +617,22 @@ template <typename R> struct EngineT : Engine {
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 1, P2, FM1>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, Cx, EX, CL, 2, P2, FM1>, x_smem))) return r;
       if ((r = smem_attr(k_c2r_x_exp_cnx<R, R, EX, CL, 3, P2, FM1>, x_smem))) return r;
+      if constexpr (sizeof(R) == 4 && P2) {
+        p1_pipe = !rpsi && !(p.flags & DGPE_FLAG_P1_ONESHOT);
+        if (p1_pipe) {
+          // as many persistent CTAs as fit, at most one per tile
+          p1_smem[0] = p1_smem_layout<R>(nx, ny, nz, x_LP, px, x_pitchz, x_pitch, CL).total;
+          p1_smem[1] = p1_smem_layout<Cx>(nx, ny, nz, x_LP, px, x_pitchz, x_pitch, CL).total;
+          if ((r = smem_attr(k_p1_pipe<R, EX, CL>, p1_smem[0]))) return r;
+          if ((r = smem_attr(k_p1_pipe<Cx, EX, CL>, p1_smem[1]))) return r;
+          int occ0 = 0, occ1 = 0;
+          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_p1_pipe<R, EX, CL>, x_T, p1_smem[0]));
+          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_p1_pipe<Cx, EX, CL>, x_T, p1_smem[1]));
+          if (occ0 < 1 || occ1 < 1) p1_pipe = false;
+          p1_grid[0] = std::max(1, std::min(x_grid, nsm * occ0));
+          p1_grid[1] = std::max(1, std::min(x_grid, nsm * occ1));
+        }
+      }
       return DGPE_OK;
     });
     if (rc) return rc;
@@ -765,6 +788,11 @@ template <typename R> struct EngineT : Engine {
       constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       if (mode == 0 && rpsi) {
         k_c2r_x_exp_cnx<R, R, EX, CL, 4, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
+      } else if (mode == 0 && p1_pipe) {
+        if constexpr (sizeof(R) == 4 && P2) {
+          if (imag) k_p1_pipe<R, EX, CL><<<p1_grid[0], x_T, p1_smem[0], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
+          else k_p1_pipe<Cx, EX, CL><<<p1_grid[1], x_T, p1_smem[1], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
+        }
       } else if (mode == 0) {
         if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
         else k_c2r_x_exp_cnx<R, Cx, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
@@ -998,7 +1026,18 @@ template <typename R> struct EngineT : Engine {
     const double one = 1.0, zero = 0.0;
     DGPE_CK(cudaMemcpyAsync(prm + PRM_SC, &one, sizeof(double), cudaMemcpyHostToDevice, s));
     DGPE_CK(cudaMemcpyAsync(prm + PRM_NONFINITE, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+    DGPE_CK(cudaMemcpyAsync(prm + PRM_TIMEOUT, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
     DGPE_CK(cudaStreamSynchronize(s));
+    return DGPE_OK;
+  }
+  int wait_status(cudaStream_t s) override {
+    double f = 0.0;
+    DGPE_CK(cudaMemcpyAsync(&f, prm + PRM_TIMEOUT, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DGPE_CK(cudaStreamSynchronize(s));
+    if (f != 0.0) {
+      err = "a bounded device-side wait ran out (the step's results are incomplete)";
+      return DGPE_ETIMEOUT;
+    }
     return DGPE_OK;
   }
   int set_psi_host(const double *src, cudaStream_t s) override {
@@ -1077,6 +1116,10 @@ template <typename R> struct EngineT : Engine {
     DGPE_CK(cudaMemcpyAsync(hp, prm, sizeof(hp), cudaMemcpyDeviceToHost, s));
     DGPE_CK(cudaMemcpyAsync(&st, dstep, sizeof(st), cudaMemcpyDeviceToHost, s));
     DGPE_CK(cudaStreamSynchronize(s));
+    if (hp[PRM_TIMEOUT] != 0.0) {
+      err = "a bounded device-side wait ran out (the step's results are incomplete)";
+      return DGPE_ETIMEOUT;
+    }
     if (h[OBS_BAD] > 0.0 || hp[PRM_NONFINITE] != 0.0) {
       err = "state holds NaN or Inf";
       return DGPE_ENONFINITE;

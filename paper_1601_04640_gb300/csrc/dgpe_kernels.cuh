@@ -31,6 +31,7 @@ enum {
   PRM_M = 5,     // number of trap-modulation coefficients
   PRM_CM = 6,    // c_1 .. c_16
   PRM_NONFINITE = 22,  // set to 1 by the norm finaliser when the norm is not finite
+  PRM_TIMEOUT = 23,    // set to 1 by a kernel whose bounded device-side wait ran out
   PRM_COUNT = 24
 };
 
@@ -323,9 +324,13 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   const int T = blockDim.x, t = threadIdx.x;
   auto row_of = [&](int idx) { return POW2 ? (idx >> ln) : (idx / n); };
   auto col_of = [&](int idx) { return POW2 ? (idx & (n - 1)) : (idx % n); };
-  if (t < 2 * A.LP) {
-    const int row = 2 * p0 + t;
-    s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
+  // the trap tables are read only by the modes that apply the exponential
+  // (MODE 1 and 2 callers may leave vx, vy, vz NULL)
+  if constexpr (MODE != 1 && MODE != 2) {
+    if (t < 2 * A.LP) {
+      const int row = 2 * p0 + t;
+      s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
+    }
   }
   // x twiddles: read from global memory here (a shared copy measured slower
   // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM);
@@ -367,7 +372,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
     }
   }
   if (t == 0) {
-    s_k[0] = (R)(trap_dts(A.prm, *A.step) * A.dtf);
+    s_k[0] = (MODE != 1 && MODE != 2) ? (R)(trap_dts(A.prm, *A.step) * A.dtf) : (R)0;
     s_k[1] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_G]);
     s_k[2] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_GDD]);
     s_k[3] = (R)A.prm[PRM_SC];
@@ -486,6 +491,151 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_ba
   __shared__ XArgs<R> sA;
   const XArgs<R> &A = block_args(args, sA);
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
+}
+
+// ----------------------------------------------- P1, FP32 pipelined form
+// The x-line pass of the FP32 bulk (complex state, power-of-two nx) as a
+// persistent pipeline.  A tile is the 2 LP consecutive rows of psi and of the
+// half spectrum that the one-shot kernel above gives a CTA; both are
+// contiguous blocks, so one thread brings them into shared memory with two
+// bulk copies that complete on an mbarrier (no per-element load
+// instructions), and the next tile's copies are issued as soon as the
+// current tile's C2R transform and exponential have consumed the staged data,
+// so they overlap its Crank-Nicolson solve and store.  The Z tile of the C2R
+// transform reuses the spectrum's staging buffer (every Stockham stage reads
+// all of its inputs before a barrier and writes after it).  The tables (CN
+// m, alpha, P, Q; the trap potentials) are staged once per CTA.  Shared
+// memory (dynamic): psi stage [2 LP][nx], spectrum stage / Z tile,
+// padded psi tile [2 LP][pitch], CN tables, V_x, V_y, V_z.
+struct P1Smem {
+  size_t sp, sz, pt, tab, vx, vy, vz, total;  // byte offsets
+};
+__host__ __device__ inline size_t p1_align16(size_t b) { return (b + 15) & ~(size_t)15; }
+template <typename Coef>
+__host__ __device__ inline P1Smem p1_smem_layout(int nx, int ny, int nz, int LP, int px, int pitchz, int pitch, int CL) {
+  P1Smem L;
+  const int rows = 2 * LP;
+  const size_t zel = (size_t)((rows * px > LP * pitchz) ? rows * px : LP * pitchz);
+  L.sp = 0;
+  L.sz = p1_align16(L.sp + sizeof(float2) * (size_t)rows * nx);
+  L.pt = p1_align16(L.sz + sizeof(float2) * zel);
+  L.tab = p1_align16(L.pt + sizeof(float2) * (size_t)rows * pitch);
+  L.vx = p1_align16(L.tab + sizeof(Coef) * 4 * (size_t)(nx + nx / CL + 1));
+  L.vy = p1_align16(L.vx + sizeof(float) * (size_t)nx);
+  L.vz = p1_align16(L.vy + sizeof(float) * (size_t)ny);
+  L.total = p1_align16(L.vz + sizeof(float) * (size_t)nz);
+  return L;
+}
+#ifndef DGPE_WAIT_LIMIT
+#define DGPE_WAIT_LIMIT (1 << 22)  // polls of a bounded mbarrier wait
+#endif
+template <typename Coef, int EPT, int CL>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant__ XArgs<float> A, int ntiles, int nz,
+                                                         double *timeout_flag) {
+  typedef float R;
+  typedef float2 Cx;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  constexpr int PW = Pad<R>::W;
+  const int n = A.nx, nrows = A.nrows, P = A.pitch, LP = A.LP, px = A.px, ny = A.ny;
+  const int rows = 2 * LP;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int ln = ilog2(n);
+  const P1Smem Ly = p1_smem_layout<Coef>(n, ny, nz, LP, px, A.pitchz, P, CL);
+  Cx *const sp = reinterpret_cast<Cx *>(smraw + Ly.sp);
+  Cx *const sz = reinterpret_cast<Cx *>(smraw + Ly.sz);
+  Cx *const pt = reinterpret_cast<Cx *>(smraw + Ly.pt);
+  Coef *const tab = reinterpret_cast<Coef *>(smraw + Ly.tab);
+  R *const svx = reinterpret_cast<R *>(smraw + Ly.vx);
+  R *const svy = reinterpret_cast<R *>(smraw + Ly.vy);
+  R *const svz = reinterpret_cast<R *>(smraw + Ly.vz);
+  __shared__ unsigned long long bar;
+  __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the tile's rows (2 LP <= DGPE_MAXT)
+  __shared__ R s_k[4];
+  const bool dip = A.has_dip != 0;
+  auto issue = [&](int tile) {  // thread 0
+    const int r0 = tile * rows;
+    const int nr = (nrows - r0 < rows) ? nrows - r0 : rows;
+    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * n);
+    const unsigned bs = dip ? (unsigned)(sizeof(Cx) * (size_t)nr * px) : 0u;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar, bp + bs);
+    bulk_g2s(sp, A.psi + (size_t)r0 * n, bp, &bar);
+    if (dip) bulk_g2s(sz, A.spec + (size_t)r0 * px, bs, &bar);
+  };
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    s_k[0] = (R)(trap_dts(A.prm, *A.step) * A.dtf);
+    s_k[1] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_G]);
+    s_k[2] = (R)(A.prm[PRM_DT] * A.dtf * A.prm[PRM_GDD]);
+    s_k[3] = (R)A.prm[PRM_SC];
+  }
+  __syncthreads();
+  if (t == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+  stage_cn_tables<Coef, CL>(tab, reinterpret_cast<const Coef *>(A.cntab), n);
+  for (int i = t; i < n; i += T) svx[i] = A.vx[i];
+  for (int i = t; i < ny; i += T) svy[i] = A.vy[i];
+  for (int i = t; i < nz; i += T) svz[i] = A.vz[i];
+  __syncthreads();
+  const R dts = s_k[0], gdt = s_k[1], gdddt = s_k[2], sc = s_k[3];
+  const int imag = A.imag;
+  const int nh = n / 2;
+  const cx<R> *s_twp = A.tw;
+  unsigned phase = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
+    const int r0 = tile * rows;
+    // every thread polls the barrier; the block then agrees on the outcome
+    const bool ok = mbar_wait_bounded(&bar, phase, DGPE_WAIT_LIMIT);
+    if (t < rows) {
+      const int row = r0 + t;
+      s_vyz[t] = (row < nrows) ? svy[row % ny] + svz[row / ny] : (R)0;
+    }
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) *timeout_flag = 1.0;
+      return;
+    }
+    // exponential substep: staged psi (dense) -> padded tile
+    auto apply_e = [&](int L, int a, R phi) {
+      const cx<R> v = cscale(sp[(L << ln) + a], sc);
+      const R dens = v.x * v.x + v.y * v.y;
+      const R th = dts * (svx[a] + s_vyz[L]) + gdt * dens + gdddt * phi;
+      pt[L * P + a + a / CL] = nonlinear_factor<R>(v, th, imag);
+    };
+    if (dip) {
+      auto load = [&](int l, int a) -> cx<R> {
+        const int k = (a <= nh) ? a : n - a;
+        cx<R> X0 = czero<cx<R>>(), X1 = czero<cx<R>>();
+        if (r0 + 2 * l < nrows) X0 = sz[(2 * l) * px + k];
+        if (r0 + 2 * l + 1 < nrows) X1 = sz[(2 * l + 1) * px + k];
+        if (a == 0 || a == nh) { X0.y = 0; X1.y = 0; }  // real-to-real ends of a real line
+        if (a > nh) { X0.y = -X0.y; X1.y = -X1.y; }    // Hermitian extension
+        return mk<R>(X0.x - X1.y, X0.y + X1.x);        // Z = X0 + i X1
+      };
+      auto store = [&](int l, int a, cx<R> v) {
+        apply_e(2 * l, a, v.x);
+        apply_e(2 * l + 1, a, v.y);
+      };
+      tile_fft<R, EPT, true, false, PW, true, false>(sz, A.pitchz, 1, LP, A.pl, s_twp, load, store, nullptr);
+    } else {
+      for (int idx = t; idx < rows * n; idx += T) apply_e(idx >> ln, idx & (n - 1), (R)0);
+      __syncthreads();
+    }
+    // the staged blocks are consumed: fetch the next tile behind the solve
+    const int next = tile + gridDim.x;
+    if (t == 0 && next < ntiles) issue(next);
+    // Crank-Nicolson along x: TPL lanes per line
+    const int l = t / A.TPL, q = t - l * A.TPL;
+    cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), tab, (r0 + l) < nrows);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < CL; ++i) {
+      const int idx = t + i * T;
+      const int L = idx >> ln, a = idx & (n - 1);
+      const int row = r0 + L;
+      if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
+    }
+  }
+  __syncthreads();
+  if (t == 0) mbar_inval(&bar);
 }
 
 // ------------------------------------------------- P5 / P6 / P7 (strided)

@@ -193,6 +193,10 @@ extern "C" int dgpe_dipolar_potential_noalloc(const void *psi, void *phi, int fp
   using namespace dgpe;
   if (!psi || !phi || !n || !h) { set_err("NULL argument"); return DGPE_EINVAL; }
   if (dim != 2 && dim != 3) { set_err("dim must be 2 or 3"); return DGPE_EINVAL; }
+  if (kernel == DGPE_KERNEL_QUASI2D_XZ) {
+    set_err("the quasi-2D XZ kernel is not supported by this entry point");
+    return DGPE_EUNSUPPORTED;
+  }
   if ((kernel == DGPE_KERNEL_DIPOLAR_3D && dim != 3) ||
       (kernel == DGPE_KERNEL_QUASI2D_XY && (dim != 2 || !(qd > 0.0))) ||
       (kernel != DGPE_KERNEL_DIPOLAR_3D && kernel != DGPE_KERNEL_QUASI2D_XY)) {
@@ -211,9 +215,13 @@ extern "C" int dgpe_dipolar_potential_noalloc(const void *psi, void *phi, int fp
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     set_err("cudaGetDevice", cudaGetErrorString(e));
     return DGPE_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_err("device index above 63: this entry point serves devices 0..63");
+    return DGPE_EUNSUPPORTED;
   }
   void *base = nullptr;
   {

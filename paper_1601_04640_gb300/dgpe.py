@@ -38,6 +38,7 @@ DGPE_FLAG_CN_SERIAL = 2
 DGPE_FLAG_CN_CHUNKED = 4
 DGPE_FLAG_STRANG = 8
 DGPE_FLAG_REAL_PSI = 16
+DGPE_FLAG_P1_ONESHOT = 32
 
 EXPORTS = [
     "dgpe_create", "dgpe_destroy", "dgpe_set_psi", "dgpe_get_psi", "dgpe_set_psi_device",
@@ -133,7 +134,8 @@ def _check(rc, h=None):
 
 
 def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
-                kernel=None, qd=0.5, graph=True, cn=None, plane=None, split="lie", real_psi=False):
+                kernel=None, qd=0.5, graph=True, cn=None, plane=None, split="lie", real_psi=False,
+                flags=0):
     """cn: None (automatic), "serial" or "chunked" (FP64 Crank-Nicolson form).
     split: "lie" (the paper's first-order step) or "strang" (second order,
     real time).  real_psi: hold the state as a real field (imaginary time).
@@ -169,6 +171,7 @@ def make_params(dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
         raise ValueError("split must be 'lie' or 'strang'")
     if real_psi:
         p.flags |= DGPE_FLAG_REAL_PSI
+    p.flags |= int(flags)
     return p
 
 
@@ -289,12 +292,12 @@ class Solver:
 
     def __init__(self, dim, n, h, nu, g=0.0, gdd=0.0, dt=1e-3, imag=False, fp64=True,
                  kernel=None, qd=0.5, graph=True, stream: int = 0, cn=None, split="lie",
-                 real_psi=False):
+                 real_psi=False, flags=0):
         self.dim = dim
         self.n = tuple(n)
         self.shape = (n[2], n[1], n[0]) if dim == 3 else (n[1], n[0])
         self.params = make_params(dim, n, h, nu, g, gdd, dt, imag, fp64, kernel, qd, graph, cn,
-                                  split=split, real_psi=real_psi)
+                                  split=split, real_psi=real_psi, flags=flags)
         self.h = dgpe_create(self.params, stream)
 
     def close(self):

@@ -29,6 +29,10 @@ def test_reference_arm_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "32^3" in d["config"]["workload"]
+    # the same config dict the GPU arm prints for the workload (one GPU, FP64 line)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.workload_config(bench.WORKLOADS["imag3d"], "fp64", 1)
 
 
 def test_reference_arm_unavailable_for_the_batched_sweep():

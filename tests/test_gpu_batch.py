@@ -51,6 +51,38 @@ def test_batch_matches_single_and_oracle():
         assert abs(obs[i]["mu"] - r["mu"]) <= 1e-6 * abs(r["mu"])
 
 
+def test_batch_full_length_against_oracle():
+    """The batched workload's own length: 8 problems of the seed-4640 sweep,
+    one of each size {64, ..., 512}^2 plus one more, four in imaginary and four
+    in real time, 1000 steps, every problem against the oracle at the
+    FP32-bulk bounds (relative L2 of psi 1e-5, mu 1e-6)."""
+    gbuild.build()
+    probs = synth.batched_problems(4640, 8, sizes=synth.BATCH_SIZES)
+    for i, n in enumerate(synth.BATCH_SIZES):
+        probs[i]["n"] = (n, n)
+    assert {q["imag"] for q in probs} == {True, False}
+    steps = 1000
+    with dgpe.Batch(probs) as B:
+        for i, q in enumerate(probs):
+            B.set_psi(i, _psi0(q))
+        B.step(steps)
+        outs = [B.get_psi(i) for i in range(len(probs))]
+        obs = [B.observables(i) for i in range(len(probs))]
+    worst = 0.0
+    for i, q in enumerate(probs):
+        op = oracle.Params(dim=2, n=q["n"], h=q["h"], nu=q["nu"], g=q["g"], gdd=q["gdd"], dt=q["dt"],
+                           imag=q["imag"], kernel="quasi2d", qd=q["qd"])
+        ref = oracle.step(op, _psi0(q), 0, steps)
+        e = np.linalg.norm(outs[i] - ref) / np.linalg.norm(ref)
+        r = oracle.observables(op, ref, steps)
+        worst = max(worst, e)
+        print(i, q["n"], "imag" if q["imag"] else "real", "g %.1f g_dd %.1f" % (q["g"], q["gdd"]),
+              "rel L2", e, "mu", obs[i]["mu"], r["mu"])
+        assert e < 1e-5
+        assert abs(obs[i]["mu"] - r["mu"]) <= 1e-6 * abs(r["mu"])
+    print("worst rel L2 over the batch", worst)
+
+
 def test_batch_rejects_bad_problems():
     gbuild.build()
     q = dict(n=(64, 32), h=(0.2, 0.2), nu=(1.0, 1.0), g=10.0, gdd=1.0, dt=1e-3, imag=True, qd=0.5)

@@ -137,7 +137,10 @@ def test_cubic_symmetry_zero_energy():
     assert abs(np.sum(phi * dens)) < 1e-12 * np.sum(np.abs(phi * dens))
 
 
-@pytest.mark.parametrize("k", [0.0, 0.3, 1.0, 2.5, 7.0, 20.0])
+# k d / sqrt(2) reaches the asymptotic erfcx branch (u >= 25) from k = 40 at
+# d = 1 and k = 80 at d = 0.5 (the corner of a 128^2 grid at h = 0.05 has
+# k = 88.9)
+@pytest.mark.parametrize("k", [0.0, 0.3, 1.0, 2.5, 7.0, 20.0, 40.0, 60.0, 80.0, 120.0])
 @pytest.mark.parametrize("d", [0.5, 1.0])
 def test_quasi2d_kernel_vs_quadrature(k, d):
     """U2(k) = int dkz/(2pi) (4pi/3)(3 kz^2/(k^2 + kz^2) - 1) exp(-kz^2 d^2/2)."""
@@ -158,7 +161,8 @@ def test_quasi2d_single_mode():
     assert np.max(np.abs(phi - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("kx,kz", [(0.0, 0.4), (0.7, 0.0), (1.0, 1.0), (0.3, 2.5), (5.0, 3.0), (12.0, 20.0)])
+@pytest.mark.parametrize("kx,kz", [(0.0, 0.4), (0.7, 0.0), (1.0, 1.0), (0.3, 2.5), (5.0, 3.0), (12.0, 20.0),
+                                   (60.0, 60.0), (0.0, 90.0), (20.0, 80.0), (62.8, 31.4)])
 @pytest.mark.parametrize("d", [0.5, 1.0])
 def test_quasi2d_xz_kernel_vs_quadrature(kx, kz, d):
     """XZ plane, dipoles along z in the plane, transverse profile in y:
@@ -199,3 +203,59 @@ def test_quasi2d_xz_single_modes():
     # dipoles along z in the plane: the kernel is positive for wave vectors
     # along the dipoles and negative across them
     assert oracle.q2dxz_value(0.0, kz, d) > 0 > oracle.q2dxz_value(kx, 0.0, d)
+
+
+@pytest.mark.parametrize("u", [0.0, 1e-3, 0.5, 3.0, 10.0, 24.0, 24.999, 25.0, 25.001, 26.0, 30.0, 45.0,
+                               88.9, 300.0, 1e4])
+def test_erfcx_vs_library(u):
+    """exp(u^2) erfc(u) of the quasi-2D kernels against scipy's erfcx on both
+    sides of u = 25, where the oracle switches from the direct product to the
+    asymptotic series.  Near u = 25 the direct product carries the rounding
+    of u^2 in exp (about 625 x 1.1e-16 relative); above it the series is
+    held to 2e-15, which its sixth term (2.7e-15 at u = 25) still exceeds."""
+    ref = special.erfcx(u)
+    assert abs(oracle.erfcx(u) - ref) <= (2e-13 if u < 25.0 else 2e-15) * ref
+
+
+@pytest.mark.parametrize("d", [0.5, 1.0])
+def test_quasi2d_kernels_continuous_at_branch(d):
+    """Both kernels are smooth in k: just below and just above the k where
+    u = k d / sqrt(2) crosses 25 the values agree to the derivative times the
+    gap (a dropped or mis-signed term of the series would leave a jump of
+    3 pref / q^2 ~ 2e-3 relative, the third term one of ~2e-6)."""
+    k0 = 25.0 * math.sqrt(2.0) / d
+    dk = 1e-12 * k0  # slope x gap: ~1e-14 relative
+    lo, hi = oracle.q2d_value(k0 - dk, d), oracle.q2d_value(k0 + dk, d)
+    assert abs(hi - lo) < 3e-13 * abs(lo)
+    for ang in (0.3, 0.8, 1.2):  # XZ on rays through the branch circle
+        a = (k0 - dk) * math.cos(ang), (k0 - dk) * math.sin(ang)
+        b = (k0 + dk) * math.cos(ang), (k0 + dk) * math.sin(ang)
+        lo, hi = oracle.q2dxz_value(*a, d), oracle.q2dxz_value(*b, d)
+        assert abs(hi - lo) < 3e-13 * max(abs(lo), (4 * math.pi / 3) / (math.sqrt(2 * math.pi) * d))
+
+
+def test_asymptotic_region_carries_weight_on_128_grid():
+    """The GPU parity case on a 128^2 grid at h = 0.05, d = 0.5 checks the
+    asymptotic branch only if the density has weight where u >= 25.  Planting
+    mistakes in the oracle's U table there (on the CPU) shows it does: a
+    flipped 1/q^2 term moves Phi_d by > 1e-5 (the FP32-bulk bound) and a 1e-6
+    relative error by > 1e-10 (far above the FP64 bound)."""
+    n, h, d = (128, 128), (0.05, 0.05), 0.5
+    psi = synth.gaussian_state(n, h, (1.0, 1.5), 0.05, 11)
+    dens = np.abs(psi) ** 2
+    U = oracle.kernel_q2d(n, h, d)
+    kx = 2 * np.pi * np.fft.fftfreq(n[0], h[0])
+    ky = 2 * np.pi * np.fft.fftfreq(n[1], h[1])
+    KX, KY = np.meshgrid(kx, ky)
+    q = np.hypot(KX, KY) * d
+    mask = q / math.sqrt(2) >= 25
+    assert 0.05 < mask.mean() < 0.2
+    pref = (4 * math.pi / 3) / (math.sqrt(2 * math.pi) * d)
+    F = np.fft.fft2(dens)
+    phi = np.real(np.fft.ifft2(U * F))
+    bad = U.copy()
+    bad[mask] -= pref * 6 / q[mask] ** 2
+    assert np.linalg.norm(np.real(np.fft.ifft2(bad * F)) - phi) > 1e-5 * np.linalg.norm(phi)
+    bad = U.copy()
+    bad[mask] *= 1 + 1e-6
+    assert np.linalg.norm(np.real(np.fft.ifft2(bad * F)) - phi) > 1e-10 * np.linalg.norm(phi)

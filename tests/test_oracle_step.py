@@ -196,3 +196,25 @@ def test_imaginary_time_keeps_a_real_state_real(dim):
     assert np.max(np.abs(out.real)) > 0.0
     p.imag = False
     assert np.max(np.abs(oracle.step(p, psi, 0, 1).imag)) > 1e-6
+
+
+def test_divergence_golden_first_checkpoint_reproduces():
+    """tests/golden/divergence_64.json came from the oracle: its first
+    checkpoint (100 steps, 2^-24 noise after every step) is re-derived here."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "divergence_64.json")
+    with open(path) as f:
+        gold = json.load(f)
+    assert gold["checkpoints"][0] == 100
+    n, h, nu = (64, 64, 64), (0.2,) * 3, (1.0, 1.0, 0.5)
+    op = oracle.Params(dim=3, n=n, h=h, nu=nu, g=150, gdd=60, dt=5e-4, imag=False, kernel="dipolar3d")
+    psi0 = synth.gaussian_state(n, h, (0.8, 0.8, 0.4), 0.01, 9)
+    base = oracle.step(op, psi0, 0, 100)
+    psi, eps = psi0, gold["fp32_rounding"]["eps"]
+    for s in range(100):
+        psi = oracle.step(op, psi, s, 1)
+        xi, _ = synth.normal_pairs(77 + s, psi.size)
+        psi = psi * (1.0 + eps * xi.reshape(psi.shape))
+    d = float(np.linalg.norm(psi - base) / np.linalg.norm(base))
+    assert abs(d / gold["fp32_rounding"]["every_step"][0] - 1) < 1e-6
