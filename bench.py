@@ -2,9 +2,10 @@
 FP32-bulk forms) and the fraction of the HBM roofline of the dominant kernel.
 
 Workload (default): real-time 256^3 grid, spacing 0.1, cigar trap
-V = (x^2 + y^2 + 0.25 z^2)/2, g_dd = 60, dt = 5e-4; the state is an
-imaginary-time ground state at g = 200 (prepared on the GPU, untimed) and g is
-quenched to 150 before the timed steps.  One step = one full split step over
+V = (x^2 + y^2 + 0.25 z^2)/2, g_dd = 60, dt = 5e-4; the state is relaxed
+towards the ground state at g = 200 by 400 imaginary-time steps (FP32 bulk,
+dt = 2e-3, on the GPU, untimed; not converged) and g is quenched to 150 before
+the timed steps.  One step = one full split step over
 the grid (all passes).  Inputs are synthetic (seeded Gaussian + 1% noise).
 
 `python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]`
@@ -31,7 +32,7 @@ WORKLOADS = {
     "real3d": dict(n=(256, 256, 256), h=(0.1, 0.1, 0.1), nu=(1.0, 1.0, 0.5), g_prep=200.0, g=150.0,
                    gdd=60.0, dt=5e-4, widths=(1.0, 1.0, 0.5), seed=2016, prep_steps=400,
                    desc="real3d 256^3, h=0.1, cigar nu=(1,1,0.5), g 200->150 quench, g_dd=60, dt=5e-4, "
-                        "real time from the imaginary-time ground state"),
+                        "real time from a 400-step imaginary-time relaxation at g=200 (not converged)"),
     "large": dict(n=(512, 512, 256), h=(0.08, 0.08, 0.08), nu=(1.0, 1.0, 3.0), g_prep=None, g=500.0,
                   gdd=200.0, dt=2e-4, widths=(1.0, 1.0, 3.0), seed=2016, prep_steps=0,
                   desc="large real3d 512x512x256, h=0.08, pancake nu=(1,1,3), g=500, g_dd=200, "
@@ -50,7 +51,7 @@ WORKLOADS = {
                  metric="2D XZ split-step site-updates/s (FP64 vs FP32-bulk) and % of HBM roofline",
                  desc="2D XZ plane 512x512, h=0.05, nu=(1,2), dipoles along z in the plane, quasi-2D "
                       "XZ kernel d=0.5, g 200->150 quench, g_dd=60, dt=5e-4, real time from the "
-                      "imaginary-time ground state"),
+                      "200-step imaginary-time relaxation at g=200 (not converged)"),
     "imag256": dict(n=(256, 256, 256), h=(0.1, 0.1, 0.1), nu=(1.0, 1.0, 0.5), g_prep=None, g=200.0,
                     gdd=60.0, dt=2e-3, widths=(1.0, 1.0, 0.5), seed=2018, prep_steps=0, imag=True,
                     real_init=True,
@@ -272,7 +273,7 @@ def main():
     hbm_peak, peak_kind = peaks()
     imag = wl.get("imag", False)
 
-    # ground state (imaginary time at g_prep), prepared once in FP32-bulk
+    # relaxation towards the ground state (imaginary time at g_prep), FP32-bulk
     psi0 = synth.gaussian_state(n, wl["h"], wl["widths"], 0.01, wl["seed"])
     if wl.get("real_init"):
         psi0 = psi0.real.astype(np.complex128)

@@ -113,10 +113,11 @@ extern "C" {
                                    real time (at create and in dgpe_set_mode)
                                    and the batched form. */
 
-#define DGPE_FLAG_P1_ONESHOT 32u /* FP32 bulk: run the x-line pass (C2R, exponential,
-                                   CN_x) as one CTA per tile instead of the
-                                   default persistent CTAs fed by bulk
-                                   asynchronous copies (same arithmetic) */
+#define DGPE_FLAG_P1_ONESHOT 32u /* FP32 bulk: run the two x-line passes
+                                   (density + R2C; C2R, exponential, CN_x) as
+                                   one CTA per tile instead of the default
+                                   persistent CTAs fed by bulk asynchronous
+                                   copies (same arithmetic) */
 
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */

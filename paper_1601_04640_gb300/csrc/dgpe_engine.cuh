@@ -205,6 +205,10 @@ template <typename R> struct EngineT : Engine {
   bool p1_pipe = false;
   int p1_grid[2] = {0, 0};  // real, complex CN coefficients
   size_t p1_smem[2] = {0, 0};
+  // ... and the pipelined density / R2C pass (k_p4_pipe)
+  bool p4_pipe = false;
+  int p4_grid = 0;
+  size_t p4_smem = 0;
   struct CnCfg {
     int n, ncols, W, TPL, C, pitch, T;
     long long es, os;
@@ -632,6 +636,15 @@ template <typename R> struct EngineT : Engine {
           p1_grid[0] = std::max(1, std::min(x_grid, nsm * occ0));
           p1_grid[1] = std::max(1, std::min(x_grid, nsm * occ1));
         }
+        p4_pipe = !rpsi && !(p.flags & DGPE_FLAG_P1_ONESHOT);
+        if (p4_pipe) {
+          p4_smem = sizeof(Cx) * (2 * (size_t)2 * x_LP * nx + (size_t)x_LP * x_pitchz);
+          if ((r = smem_attr(k_p4_pipe<EX>, p4_smem))) return r;
+          int occ = 0;
+          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_p4_pipe<EX>, x_T, p4_smem));
+          if (occ < 1) p4_pipe = false;
+          p4_grid = std::max(1, std::min(x_grid, nsm * occ));
+        }
       }
       return DGPE_OK;
     });
@@ -761,7 +774,9 @@ template <typename R> struct EngineT : Engine {
       constexpr bool FM1 = P2 && sizeof(R) == 8;  // the C2R pass: FP64 only
       if (dens_in) k_dens_r2c_x<R, EX, 1, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       else if (rpsi && !src) k_dens_r2c_x<R, EX, 2, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
-      else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
+      else if (p4_pipe) {
+        if constexpr (sizeof(R) == 4 && P2) k_p4_pipe<EX><<<p4_grid, x_T, p4_smem, s>>>(A, x_grid, prm + PRM_TIMEOUT);
+      } else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
     launched(1);

@@ -493,6 +493,93 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_ba
   c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
 }
 
+#ifndef DGPE_WAIT_LIMIT
+#define DGPE_WAIT_LIMIT (1 << 22)  // polls of a bounded mbarrier wait
+#endif
+
+// ----------------------------------------------- P4, FP32 pipelined form
+// The density + R2C pass of the FP32 bulk (complex state, power-of-two nx) as
+// a persistent pipeline: a tile's 2 LP rows of psi are one contiguous block,
+// brought into one of two staging buffers by a bulk copy on that buffer's
+// mbarrier, two tiles ahead of the transform.  The density is formed as the
+// first Stockham stage reads the staged rows; the separated half spectra are
+// stored from the Z tile.  Shared memory (dynamic): 2 psi stages [2 LP][nx],
+// Z tile [LP][pitchz].
+template <int EPT>
+__global__ void __launch_bounds__(DGPE_MAXT, 2) k_p4_pipe(const __grid_constant__ XArgs<float> A, int ntiles,
+                                                         double *timeout_flag) {
+  typedef float R;
+  typedef float2 Cx;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int PW = Pad<R>::W;
+  const int n = A.nx, nrows = A.nrows, LP = A.LP, px = A.px, SL = A.pitchz;
+  const int rows = 2 * LP;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int ln = ilog2(n);
+  Cx *const stg[2] = {reinterpret_cast<Cx *>(smraw), reinterpret_cast<Cx *>(smraw) + (size_t)rows * n};
+  Cx *const zt = reinterpret_cast<Cx *>(smraw) + 2 * (size_t)rows * n;
+  __shared__ unsigned long long bar[2];
+  __shared__ R s_sc2;
+  __shared__ __align__(16) Cx s_tw[512];
+  auto issue = [&](int tile, int k) {  // thread 0
+    const int r0 = tile * rows;
+    const int nr = (nrows - r0 < rows) ? nrows - r0 : rows;
+    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * n);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[k], bp);
+    bulk_g2s(stg[k], A.psi + (size_t)r0 * n, bp, &bar[k]);
+  };
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    const R sc = (R)A.prm[PRM_SC];
+    s_sc2 = sc * sc;
+  }
+  __syncthreads();
+  if (t == 0) {
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+  for (int i = t; i < n; i += T) s_tw[i] = A.tw[i];
+  __syncthreads();
+  const R sc2 = s_sc2;
+  const int nh = n / 2 + 1;
+  unsigned ph[2] = {0u, 0u};
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
+    const int r0 = tile * rows;
+    const bool ok = mbar_wait_bounded(&bar[k], ph[k], DGPE_WAIT_LIMIT);
+    ph[k] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) *timeout_flag = 1.0;
+      return;
+    }
+    const Cx *__restrict__ sp = stg[k];
+    auto load = [&](int l, int a) -> cx<R> {
+      R d0 = 0, d1 = 0;
+      if (r0 + 2 * l < nrows) { const Cx v = sp[((2 * l) << ln) + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
+      if (r0 + 2 * l + 1 < nrows) { const Cx v = sp[((2 * l + 1) << ln) + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
+      return mk<R>(d0, d1);
+    };
+    auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
+    tile_fft<R, EPT, false, false, PW, true, false>(zt, SL, 1, LP, A.pl, s_tw, load, store, nullptr);
+    // this stage is consumed: refill it two tiles ahead
+    const int next2 = tile + 2 * gridDim.x;
+    if (t == 0 && next2 < ntiles) issue(next2, k);
+    // two real lines were packed as Z = n0 + i n1
+    for (int idx = t; idx < LP * nh; idx += T) {
+      const int l = idx / nh, kk = idx - l * nh;
+      const int ra = r0 + 2 * l, rb = ra + 1;
+      if (ra >= nrows) continue;
+      const cx<R> Zk = zt[sidx<PW>(l, kk, SL, 1)], Zm = zt[sidx<PW>(l, (kk == 0 ? 0 : n - kk), SL, 1)];
+      A.spec[(size_t)ra * px + kk] = mk<R>((R)0.5 * (Zk.x + Zm.x), (R)0.5 * (Zk.y - Zm.y));
+      if (rb < nrows) A.spec[(size_t)rb * px + kk] = mk<R>((R)0.5 * (Zk.y + Zm.y), (R)0.5 * (Zm.x - Zk.x));
+    }
+  }
+  __syncthreads();
+  if (t == 0) { mbar_inval(&bar[0]); mbar_inval(&bar[1]); }
+}
+
 // ----------------------------------------------- P1, FP32 pipelined form
 // The x-line pass of the FP32 bulk (complex state, power-of-two nx) as a
 // persistent pipeline.  A tile is the 2 LP consecutive rows of psi and of the
@@ -526,15 +613,12 @@ __host__ __device__ inline P1Smem p1_smem_layout(int nx, int ny, int nz, int LP,
   L.total = p1_align16(L.vz + sizeof(float) * (size_t)nz);
   return L;
 }
-#ifndef DGPE_WAIT_LIMIT
-#define DGPE_WAIT_LIMIT (1 << 22)  // polls of a bounded mbarrier wait
-#endif
 template <typename Coef, int EPT, int CL>
 __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant__ XArgs<float> A, int ntiles, int nz,
                                                          double *timeout_flag) {
   typedef float R;
   typedef float2 Cx;
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int PW = Pad<R>::W;
   const int n = A.nx, nrows = A.nrows, P = A.pitch, LP = A.LP, px = A.px, ny = A.ny;
   const int rows = 2 * LP;
