@@ -395,6 +395,102 @@ __device__ __forceinline__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, 
   }
 }
 
+// ------------------------------- compile-time Stockham FFT over a line tile
+// The same transform as tile_fft for a line-major tile (line l, element a at
+// l SL + a + a / PADW) when the line length N, the number of lines NL, the
+// block size T and the radix sequence are compile-time constants: every
+// index (line, butterfly, twiddle, shared-memory address) folds to shifts,
+// masks and immediate offsets, and only the stages the length needs are
+// compiled.  Radices: the largest of 16, 8, 4, 2 dividing both EPT and what
+// is left of N, in order (the inverse runs the sequence reversed).
+constexpr int ct_radix(int n, int ept, int s) {
+  int m = n;
+  for (int k = 0; k < 16; ++k) {
+    int r = 0;
+    if (ept % 16 == 0 && m % 16 == 0) r = 16;
+    else if (ept % 8 == 0 && m % 8 == 0) r = 8;
+    else if (ept % 4 == 0 && m % 4 == 0) r = 4;
+    else if (m % 2 == 0) r = 2;
+    if (r == 0) return 0;
+    if (k == s) return r;
+    m /= r;
+  }
+  return 0;
+}
+constexpr int ct_nstages(int n, int ept) {
+  int s = 0, m = n;
+  while (m > 1) { m /= ct_radix(n, ept, s); ++s; }
+  return s;
+}
+constexpr int ct_log2(int v) { return v <= 1 ? 0 : 1 + ct_log2(v / 2); }
+
+template <typename R, int N, int EPT, int RAD, int NS, bool INV, int PADW, int SL, int NL, int T, bool FIRST,
+          bool LAST, class Load, class Store>
+__device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict__ tw, Load &load, Store &store) {
+  static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
+  constexpr int NB = EPT / RAD;
+  constexpr int NBL = N / RAD, LNBL = ct_log2(NBL), LR = ct_log2(RAD), LNS = ct_log2(NS);
+  constexpr int B = NBL * NL;
+  constexpr int TSTR = N / (NS * RAD);
+  const int t = threadIdx.x;
+  cx<R> v[EPT];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = t + i * T;
+    const bool ok = (B % T == 0) || b < B;
+    const int l = b >> LNBL, j = b & (NBL - 1);
+    cx<R> *u = v + i * RAD;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      const int a = j + r * NBL;
+      if (!ok) u[r] = czero<cx<R>>();
+      else if (FIRST) u[r] = load(l, a);
+      else u[r] = sm[l * SL + a + a / PADW];
+    }
+    if constexpr (!FIRST) {
+      const int k = j & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const cx<R> w = tw[k * r * TSTR];
+        u[r] = INV ? cmulconj(u[r], w) : cmul(u[r], w);
+      }
+    }
+    dft<RAD, INV>(u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = t + i * T;
+    if ((B % T == 0) || b < B) {
+      const int l = b >> LNBL, j = b & (NBL - 1);
+      const int base = ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
+      cx<R> *u = v + i * RAD;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int a = base + r * NS;
+        if (LAST) store(l, a, u[r]);
+        else sm[l * SL + a + a / PADW] = u[r];
+      }
+    }
+  }
+  __syncthreads();
+}
+template <typename R, int N, int EPT, bool INV, int PADW, int SL, int NL, int T, int S, int NSACC, class Load,
+          class Store>
+__device__ __forceinline__ void tile_fft_ct_from(cx<R> *sm, const cx<R> *__restrict__ tw, Load &load, Store &store) {
+  constexpr int NST = ct_nstages(N, EPT);
+  if constexpr (S < NST) {
+    constexpr int RAD = INV ? ct_radix(N, EPT, NST - 1 - S) : ct_radix(N, EPT, S);
+    fft_stage_ct<R, N, EPT, RAD, NSACC, INV, PADW, SL, NL, T, S == 0, S == NST - 1>(sm, tw, load, store);
+    tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, S + 1, NSACC * RAD>(sm, tw, load, store);
+  }
+}
+// Full transform of the NL lines of the tile; tw[t] = exp(-2 pi i t / N).
+template <typename R, int N, int EPT, bool INV, int PADW, int SL, int NL, int T, class Load, class Store>
+__device__ __forceinline__ void tile_fft_ct(cx<R> *sm, const cx<R> *__restrict__ tw, Load load, Store store) {
+  tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, 0, 1>(sm, tw, load, store);
+}
+
 // ------------------------------------------- Crank-Nicolson (Thomas) solve
 // One CN substep along a line of n points, in increment form:
 //   x = psi + w,  A w = r,  r = -2 kt (2 psi_a - psi_{a-1} - psi_{a+1}),

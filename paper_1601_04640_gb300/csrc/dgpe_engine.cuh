@@ -162,6 +162,19 @@ inline double wavenumber(int j, int n, double h) {
 #ifndef DGPE_FFT_FMA_F32
 #define DGPE_FFT_FMA_F32 0  // FP32 density and strided transforms in FMA form too (measured 3 % slower)
 #endif
+// Call f(N) with N = n as a compile-time constant for the power-of-two line
+// lengths of the length-specialised kernels (0 when n is not one of them).
+template <class F> int with_pow2_len(int n, F &&f) {
+  switch (n) {
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+    case 256: return f(std::integral_constant<int, 256>{});
+    case 512: return f(std::integral_constant<int, 512>{});
+    default: return f(std::integral_constant<int, 0>{});
+  }
+}
+
 template <typename R> struct EngineT : Engine {
   typedef cx<R> Cx;
   static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFTs, power-of-two lengths
@@ -627,23 +640,45 @@ template <typename R> struct EngineT : Engine {
           // as many persistent CTAs as fit, at most one per tile
           p1_smem[0] = p1_smem_layout<R>(nx, ny, nz, x_LP, px, x_pitchz, x_pitch, CL).total;
           p1_smem[1] = p1_smem_layout<Cx>(nx, ny, nz, x_LP, px, x_pitchz, x_pitch, CL).total;
-          if ((r = smem_attr(k_p1_pipe<R, EX, CL>, p1_smem[0]))) return r;
-          if ((r = smem_attr(k_p1_pipe<Cx, EX, CL>, p1_smem[1]))) return r;
-          int occ0 = 0, occ1 = 0;
-          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_p1_pipe<R, EX, CL>, x_T, p1_smem[0]));
-          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_p1_pipe<Cx, EX, CL>, x_T, p1_smem[1]));
-          if (occ0 < 1 || occ1 < 1) p1_pipe = false;
-          p1_grid[0] = std::max(1, std::min(x_grid, nsm * occ0));
-          p1_grid[1] = std::max(1, std::min(x_grid, nsm * occ1));
+          r = with_pow2_len(nx, [&](auto Nc) -> int {
+            constexpr int N = decltype(Nc)::value;
+            if constexpr (N == 0 || CL != 16) {
+              p1_pipe = false;
+              return DGPE_OK;
+            } else {
+              int q;
+              if ((q = smem_attr(k_p1_pipe<R, EX, CL, N>, p1_smem[0]))) return q;
+              if ((q = smem_attr(k_p1_pipe<Cx, EX, CL, N>, p1_smem[1]))) return q;
+              int occ0 = 0, occ1 = 0;
+              DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_p1_pipe<R, EX, CL, N>, x_T, p1_smem[0]));
+              DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_p1_pipe<Cx, EX, CL, N>, x_T, p1_smem[1]));
+              if (occ0 < 1 || occ1 < 1) p1_pipe = false;
+              p1_grid[0] = std::max(1, std::min(x_grid, nsm * occ0));
+              p1_grid[1] = std::max(1, std::min(x_grid, nsm * occ1));
+              return DGPE_OK;
+            }
+          });
+          if (r) return r;
         }
         p4_pipe = !rpsi && !(p.flags & DGPE_FLAG_P1_ONESHOT);
         if (p4_pipe) {
           p4_smem = sizeof(Cx) * (2 * (size_t)2 * x_LP * nx + (size_t)x_LP * x_pitchz);
-          if ((r = smem_attr(k_p4_pipe<EX>, p4_smem))) return r;
-          int occ = 0;
-          DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_p4_pipe<EX>, x_T, p4_smem));
-          if (occ < 1) p4_pipe = false;
-          p4_grid = std::max(1, std::min(x_grid, nsm * occ));
+          r = with_pow2_len(nx, [&](auto Nc) -> int {
+            constexpr int N = decltype(Nc)::value;
+            if constexpr (N == 0 || CL != 16) {
+              p4_pipe = false;
+              return DGPE_OK;
+            } else {
+              int q;
+              if ((q = smem_attr(k_p4_pipe<EX, N>, p4_smem))) return q;
+              int occ = 0;
+              DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_p4_pipe<EX, N>, x_T, p4_smem));
+              if (occ < 1) p4_pipe = false;
+              p4_grid = std::max(1, std::min(x_grid, nsm * occ));
+              return DGPE_OK;
+            }
+          });
+          if (r) return r;
         }
       }
       return DGPE_OK;
@@ -775,7 +810,13 @@ template <typename R> struct EngineT : Engine {
       if (dens_in) k_dens_r2c_x<R, EX, 1, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       else if (rpsi && !src) k_dens_r2c_x<R, EX, 2, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       else if (p4_pipe) {
-        if constexpr (sizeof(R) == 4 && P2) k_p4_pipe<EX><<<p4_grid, x_T, p4_smem, s>>>(A, x_grid, prm + PRM_TIMEOUT);
+        if constexpr (sizeof(R) == 4 && P2 && decltype(CLc)::value == 16) {
+          with_pow2_len(nx, [&](auto Nc) -> int {
+            constexpr int N = decltype(Nc)::value;
+            if constexpr (N != 0) k_p4_pipe<EX, N><<<p4_grid, x_T, p4_smem, s>>>(A, x_grid, prm + PRM_TIMEOUT);
+            return 0;
+          });
+        }
       } else k_dens_r2c_x<R, EX, 0, P2, FM><<<x_grid, x_T, x4_smem, s>>>(A);
       return DGPE_OK;
     });
@@ -804,9 +845,15 @@ template <typename R> struct EngineT : Engine {
       if (mode == 0 && rpsi) {
         k_c2r_x_exp_cnx<R, R, EX, CL, 4, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);
       } else if (mode == 0 && p1_pipe) {
-        if constexpr (sizeof(R) == 4 && P2) {
-          if (imag) k_p1_pipe<R, EX, CL><<<p1_grid[0], x_T, p1_smem[0], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
-          else k_p1_pipe<Cx, EX, CL><<<p1_grid[1], x_T, p1_smem[1], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
+        if constexpr (sizeof(R) == 4 && P2 && CL == 16) {
+          with_pow2_len(nx, [&](auto Nc) -> int {
+            constexpr int N = decltype(Nc)::value;
+            if constexpr (N != 0) {
+              if (imag) k_p1_pipe<R, EX, CL, N><<<p1_grid[0], x_T, p1_smem[0], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
+              else k_p1_pipe<Cx, EX, CL, N><<<p1_grid[1], x_T, p1_smem[1], s>>>(A, x_grid, nz, prm + PRM_TIMEOUT);
+            }
+            return 0;
+          });
         }
       } else if (mode == 0) {
         if (imag) k_c2r_x_exp_cnx<R, R, EX, CL, 0, P2, FM1><<<x_grid, x_T, x_smem, s>>>(A);

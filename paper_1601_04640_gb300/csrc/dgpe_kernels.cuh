@@ -505,29 +505,29 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_ba
 // first Stockham stage reads the staged rows; the separated half spectra are
 // stored from the Z tile.  Shared memory (dynamic): 2 psi stages [2 LP][nx],
 // Z tile [LP][pitchz].
-template <int EPT>
+template <int EPT, int N>
 __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p4_pipe(const __grid_constant__ XArgs<float> A, int ntiles,
                                                          double *timeout_flag) {
   typedef float R;
   typedef float2 Cx;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int PW = Pad<R>::W;
-  const int n = A.nx, nrows = A.nrows, LP = A.LP, px = A.px, SL = A.pitchz;
-  const int rows = 2 * LP;
-  const int T = blockDim.x, t = threadIdx.x;
-  const int ln = ilog2(n);
-  Cx *const stg[2] = {reinterpret_cast<Cx *>(smraw), reinterpret_cast<Cx *>(smraw) + (size_t)rows * n};
-  Cx *const zt = reinterpret_cast<Cx *>(smraw) + 2 * (size_t)rows * n;
+  constexpr int T = DGPE_MAXT, TPL = N / 16, LP = (DGPE_MAXT / 2) / TPL, ROWS = 2 * LP;
+  constexpr int SL = N + N / PW + 1, PX = N / 2 + 2, LN = ct_log2(N), NH = N / 2 + 1;
+  const int nrows = A.nrows;
+  const int t = threadIdx.x;
+  Cx *const stg0 = reinterpret_cast<Cx *>(smraw);  // stage k at stg0 + k ROWS N
+  Cx *const zt = reinterpret_cast<Cx *>(smraw) + 2 * ROWS * N;
   __shared__ unsigned long long bar[2];
   __shared__ R s_sc2;
-  __shared__ __align__(16) Cx s_tw[512];
+  __shared__ __align__(16) Cx s_tw[N];
   auto issue = [&](int tile, int k) {  // thread 0
-    const int r0 = tile * rows;
-    const int nr = (nrows - r0 < rows) ? nrows - r0 : rows;
-    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * n);
+    const int r0 = tile * ROWS;
+    const int nr = (nrows - r0 < ROWS) ? nrows - r0 : ROWS;
+    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * N);
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[k], bp);
-    bulk_g2s(stg[k], A.psi + (size_t)r0 * n, bp, &bar[k]);
+    bulk_g2s(stg0 + k * ROWS * N, A.psi + (size_t)r0 * N, bp, &bar[k]);
   };
   if (t == 0) {
     mbar_init(&bar[0], 1);
@@ -540,40 +540,41 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p4_pipe(const __grid_constant_
     if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
     if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
   }
-  for (int i = t; i < n; i += T) s_tw[i] = A.tw[i];
+  for (int i = t; i < N; i += T) s_tw[i] = A.tw[i];
   __syncthreads();
   const R sc2 = s_sc2;
-  const int nh = n / 2 + 1;
-  unsigned ph[2] = {0u, 0u};
+  unsigned ph = 0u;  // bit k: the phase parity stage k waits for next
   int k = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
-    const int r0 = tile * rows;
-    const bool ok = mbar_wait_bounded(&bar[k], ph[k], DGPE_WAIT_LIMIT);
-    ph[k] ^= 1u;
+    const int r0 = tile * ROWS;
+    const bool ok = mbar_wait_bounded(&bar[k], (ph >> k) & 1u, DGPE_WAIT_LIMIT);
+    ph ^= 1u << k;
     if (__syncthreads_or(!ok)) {
       if (t == 0) *timeout_flag = 1.0;
       return;
     }
-    const Cx *__restrict__ sp = stg[k];
+    const Cx *__restrict__ sp = stg0 + k * ROWS * N;
+    const bool full = (r0 + ROWS <= nrows);
     auto load = [&](int l, int a) -> cx<R> {
       R d0 = 0, d1 = 0;
-      if (r0 + 2 * l < nrows) { const Cx v = sp[((2 * l) << ln) + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
-      if (r0 + 2 * l + 1 < nrows) { const Cx v = sp[((2 * l + 1) << ln) + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
+      if (full || r0 + 2 * l < nrows) { const Cx v = sp[((2 * l) << LN) + a]; d0 = sc2 * (v.x * v.x + v.y * v.y); }
+      if (full || r0 + 2 * l + 1 < nrows) { const Cx v = sp[((2 * l + 1) << LN) + a]; d1 = sc2 * (v.x * v.x + v.y * v.y); }
       return mk<R>(d0, d1);
     };
-    auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
-    tile_fft<R, EPT, false, false, PW, true, false>(zt, SL, 1, LP, A.pl, s_tw, load, store, nullptr);
+    auto store = [&](int l, int a, cx<R> v) { zt[l * SL + a + a / PW] = v; };
+    tile_fft_ct<R, N, EPT, false, PW, SL, LP, T>(zt, s_tw, load, store);
     // this stage is consumed: refill it two tiles ahead
     const int next2 = tile + 2 * gridDim.x;
     if (t == 0 && next2 < ntiles) issue(next2, k);
     // two real lines were packed as Z = n0 + i n1
-    for (int idx = t; idx < LP * nh; idx += T) {
-      const int l = idx / nh, kk = idx - l * nh;
+    for (int idx = t; idx < LP * NH; idx += T) {
+      const int l = idx / NH, kk = idx - l * NH;
       const int ra = r0 + 2 * l, rb = ra + 1;
       if (ra >= nrows) continue;
-      const cx<R> Zk = zt[sidx<PW>(l, kk, SL, 1)], Zm = zt[sidx<PW>(l, (kk == 0 ? 0 : n - kk), SL, 1)];
-      A.spec[(size_t)ra * px + kk] = mk<R>((R)0.5 * (Zk.x + Zm.x), (R)0.5 * (Zk.y - Zm.y));
-      if (rb < nrows) A.spec[(size_t)rb * px + kk] = mk<R>((R)0.5 * (Zk.y + Zm.y), (R)0.5 * (Zm.x - Zk.x));
+      const int km = (kk == 0 ? 0 : N - kk);
+      const cx<R> Zk = zt[l * SL + kk + kk / PW], Zm = zt[l * SL + km + km / PW];
+      A.spec[(size_t)ra * PX + kk] = mk<R>((R)0.5 * (Zk.x + Zm.x), (R)0.5 * (Zk.y - Zm.y));
+      if (rb < nrows) A.spec[(size_t)rb * PX + kk] = mk<R>((R)0.5 * (Zk.y + Zm.y), (R)0.5 * (Zm.x - Zk.x));
     }
   }
   __syncthreads();
@@ -613,18 +614,19 @@ __host__ __device__ inline P1Smem p1_smem_layout(int nx, int ny, int nz, int LP,
   L.total = p1_align16(L.vz + sizeof(float) * (size_t)nz);
   return L;
 }
-template <typename Coef, int EPT, int CL>
+template <typename Coef, int EPT, int CL, int N>
 __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant__ XArgs<float> A, int ntiles, int nz,
                                                          double *timeout_flag) {
   typedef float R;
   typedef float2 Cx;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int PW = Pad<R>::W;
-  const int n = A.nx, nrows = A.nrows, P = A.pitch, LP = A.LP, px = A.px, ny = A.ny;
-  const int rows = 2 * LP;
-  const int T = blockDim.x, t = threadIdx.x;
-  const int ln = ilog2(n);
-  const P1Smem Ly = p1_smem_layout<Coef>(n, ny, nz, LP, px, A.pitchz, P, CL);
+  constexpr int T = DGPE_MAXT, TPL = N / CL, LP = (DGPE_MAXT / 2) / TPL, ROWS = 2 * LP;
+  constexpr int P = N + N / CL + 1, PZ = N + N / PW + 1, PX = N / 2 + 2, LN = ct_log2(N), NHALF = N / 2;
+  static_assert(ROWS * N == CL * T, "a tile holds CL elements per thread");
+  const int nrows = A.nrows, ny = A.ny;
+  const int t = threadIdx.x;
+  const P1Smem Ly = p1_smem_layout<Coef>(N, ny, nz, LP, PX, PZ, P, CL);
   Cx *const sp = reinterpret_cast<Cx *>(smraw + Ly.sp);
   Cx *const sz = reinterpret_cast<Cx *>(smraw + Ly.sz);
   Cx *const pt = reinterpret_cast<Cx *>(smraw + Ly.pt);
@@ -633,18 +635,19 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
   R *const svy = reinterpret_cast<R *>(smraw + Ly.vy);
   R *const svz = reinterpret_cast<R *>(smraw + Ly.vz);
   __shared__ unsigned long long bar;
-  __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the tile's rows (2 LP <= DGPE_MAXT)
+  __shared__ R s_vyz[ROWS];  // V_y + V_z of the tile's rows
   __shared__ R s_k[4];
+  __shared__ __align__(16) Cx s_tw[N];
   const bool dip = A.has_dip != 0;
   auto issue = [&](int tile) {  // thread 0
-    const int r0 = tile * rows;
-    const int nr = (nrows - r0 < rows) ? nrows - r0 : rows;
-    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * n);
-    const unsigned bs = dip ? (unsigned)(sizeof(Cx) * (size_t)nr * px) : 0u;
+    const int r0 = tile * ROWS;
+    const int nr = (nrows - r0 < ROWS) ? nrows - r0 : ROWS;
+    const unsigned bp = (unsigned)(sizeof(Cx) * (size_t)nr * N);
+    const unsigned bs = dip ? (unsigned)(sizeof(Cx) * (size_t)nr * PX) : 0u;
     fence_proxy_async_smem();
     mbar_expect_tx(&bar, bp + bs);
-    bulk_g2s(sp, A.psi + (size_t)r0 * n, bp, &bar);
-    if (dip) bulk_g2s(sz, A.spec + (size_t)r0 * px, bs, &bar);
+    bulk_g2s(sp, A.psi + (size_t)r0 * N, bp, &bar);
+    if (dip) bulk_g2s(sz, A.spec + (size_t)r0 * PX, bs, &bar);
   };
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -655,21 +658,20 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
   }
   __syncthreads();
   if (t == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
-  stage_cn_tables<Coef, CL>(tab, reinterpret_cast<const Coef *>(A.cntab), n);
-  for (int i = t; i < n; i += T) svx[i] = A.vx[i];
+  stage_cn_tables<Coef, CL>(tab, reinterpret_cast<const Coef *>(A.cntab), N);
+  for (int i = t; i < N; i += T) { svx[i] = A.vx[i]; s_tw[i] = A.tw[i]; }
   for (int i = t; i < ny; i += T) svy[i] = A.vy[i];
   for (int i = t; i < nz; i += T) svz[i] = A.vz[i];
   __syncthreads();
   const R dts = s_k[0], gdt = s_k[1], gdddt = s_k[2], sc = s_k[3];
   const int imag = A.imag;
-  const int nh = n / 2;
-  const cx<R> *s_twp = A.tw;
   unsigned phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
-    const int r0 = tile * rows;
+    const int r0 = tile * ROWS;
+    const bool full = (r0 + ROWS <= nrows);
     // every thread polls the barrier; the block then agrees on the outcome
     const bool ok = mbar_wait_bounded(&bar, phase, DGPE_WAIT_LIMIT);
-    if (t < rows) {
+    if (t < ROWS) {
       const int row = r0 + t;
       s_vyz[t] = (row < nrows) ? svy[row % ny] + svz[row / ny] : (R)0;
     }
@@ -679,43 +681,46 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
     }
     // exponential substep: staged psi (dense) -> padded tile
     auto apply_e = [&](int L, int a, R phi) {
-      const cx<R> v = cscale(sp[(L << ln) + a], sc);
+      const cx<R> v = cscale(sp[(L << LN) + a], sc);
       const R dens = v.x * v.x + v.y * v.y;
       const R th = dts * (svx[a] + s_vyz[L]) + gdt * dens + gdddt * phi;
       pt[L * P + a + a / CL] = nonlinear_factor<R>(v, th, imag);
     };
     if (dip) {
       auto load = [&](int l, int a) -> cx<R> {
-        const int k = (a <= nh) ? a : n - a;
+        const int k = (a <= NHALF) ? a : N - a;
         cx<R> X0 = czero<cx<R>>(), X1 = czero<cx<R>>();
-        if (r0 + 2 * l < nrows) X0 = sz[(2 * l) * px + k];
-        if (r0 + 2 * l + 1 < nrows) X1 = sz[(2 * l + 1) * px + k];
-        if (a == 0 || a == nh) { X0.y = 0; X1.y = 0; }  // real-to-real ends of a real line
-        if (a > nh) { X0.y = -X0.y; X1.y = -X1.y; }    // Hermitian extension
-        return mk<R>(X0.x - X1.y, X0.y + X1.x);        // Z = X0 + i X1
+        if (full || r0 + 2 * l < nrows) X0 = sz[(2 * l) * PX + k];
+        if (full || r0 + 2 * l + 1 < nrows) X1 = sz[(2 * l + 1) * PX + k];
+        if (a == 0 || a == NHALF) { X0.y = 0; X1.y = 0; }  // real-to-real ends of a real line
+        if (a > NHALF) { X0.y = -X0.y; X1.y = -X1.y; }    // Hermitian extension
+        return mk<R>(X0.x - X1.y, X0.y + X1.x);           // Z = X0 + i X1
       };
       auto store = [&](int l, int a, cx<R> v) {
         apply_e(2 * l, a, v.x);
         apply_e(2 * l + 1, a, v.y);
       };
-      tile_fft<R, EPT, true, false, PW, true, false>(sz, A.pitchz, 1, LP, A.pl, s_twp, load, store, nullptr);
+      tile_fft_ct<R, N, EPT, true, PW, PZ, LP, T>(sz, s_tw, load, store);
     } else {
-      for (int idx = t; idx < rows * n; idx += T) apply_e(idx >> ln, idx & (n - 1), (R)0);
+#pragma unroll 4
+      for (int i = 0; i < CL; ++i) {
+        const int idx = t + i * T;
+        apply_e(idx >> LN, idx & (N - 1), (R)0);
+      }
       __syncthreads();
     }
     // the staged blocks are consumed: fetch the next tile behind the solve
     const int next = tile + gridDim.x;
     if (t == 0 && next < ntiles) issue(next);
     // Crank-Nicolson along x: TPL lanes per line
-    const int l = t / A.TPL, q = t - l * A.TPL;
-    cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), tab, (r0 + l) < nrows);
+    const int l = t / TPL, q = t - l * TPL;
+    cn_line_st<R, Coef, CL>(pt + l * P, N, TPL, q, make_kt<Coef>(A.tau), tab, full || (r0 + l) < nrows);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
       const int idx = t + i * T;
-      const int L = idx >> ln, a = idx & (n - 1);
-      const int row = r0 + L;
-      if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
+      const int L = idx >> LN, a = idx & (N - 1);
+      if (full || r0 + L < nrows) A.psi[(size_t)(r0 + L) * N + a] = pt[L * P + a + a / CL];
     }
   }
   __syncthreads();
