@@ -424,12 +424,20 @@ constexpr int ct_nstages(int n, int ept) {
 }
 constexpr int ct_log2(int v) { return v <= 1 ? 0 : 1 + ct_log2(v / 2); }
 
+// LINE_FAST: consecutive threads take consecutive lines (column tiles, element
+// a of line l at l + a SA); otherwise consecutive butterflies of one line
+// (line-major tiles, l SL + a + a / PADW).
+template <int PADW, int SL, int SA>
+__device__ __forceinline__ int ct_sidx(int l, int a) {
+  if constexpr (PADW > 0) return l * SL + a + a / PADW;
+  else return l * SL + a * SA;
+}
 template <typename R, int N, int EPT, int RAD, int NS, bool INV, int PADW, int SL, int NL, int T, bool FIRST,
-          bool LAST, class Load, class Store>
+          bool LAST, bool LINE_FAST, int SA, class Load, class Store>
 __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict__ tw, Load &load, Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
-  constexpr int NBL = N / RAD, LNBL = ct_log2(NBL), LR = ct_log2(RAD), LNS = ct_log2(NS);
+  constexpr int NBL = N / RAD, LNBL = ct_log2(NBL), LR = ct_log2(RAD), LNS = ct_log2(NS), LNL = ct_log2(NL);
   constexpr int B = NBL * NL;
   constexpr int TSTR = N / (NS * RAD);
   const int t = threadIdx.x;
@@ -438,14 +446,15 @@ __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict_
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     const bool ok = (B % T == 0) || b < B;
-    const int l = b >> LNBL, j = b & (NBL - 1);
+    const int l = LINE_FAST ? (b & (NL - 1)) : (b >> LNBL);
+    const int j = LINE_FAST ? (b >> LNL) : (b & (NBL - 1));
     cx<R> *u = v + i * RAD;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
       const int a = j + r * NBL;
       if (!ok) u[r] = czero<cx<R>>();
       else if (FIRST) u[r] = load(l, a);
-      else u[r] = sm[l * SL + a + a / PADW];
+      else u[r] = sm[ct_sidx<PADW, SL, SA>(l, a)];
     }
     if constexpr (!FIRST) {
       const int k = j & (NS - 1);
@@ -462,33 +471,40 @@ __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict_
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
     if ((B % T == 0) || b < B) {
-      const int l = b >> LNBL, j = b & (NBL - 1);
+      const int l = LINE_FAST ? (b & (NL - 1)) : (b >> LNBL);
+      const int j = LINE_FAST ? (b >> LNL) : (b & (NBL - 1));
       const int base = ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
       cx<R> *u = v + i * RAD;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
         const int a = base + r * NS;
         if (LAST) store(l, a, u[r]);
-        else sm[l * SL + a + a / PADW] = u[r];
+        else sm[ct_sidx<PADW, SL, SA>(l, a)] = u[r];
       }
     }
   }
   __syncthreads();
 }
-template <typename R, int N, int EPT, bool INV, int PADW, int SL, int NL, int T, int S, int NSACC, class Load,
-          class Store>
+template <typename R, int N, int EPT, bool INV, int PADW, int SL, int NL, int T, bool LINE_FAST, int SA, int S,
+          int NSACC, class Load, class Store>
 __device__ __forceinline__ void tile_fft_ct_from(cx<R> *sm, const cx<R> *__restrict__ tw, Load &load, Store &store) {
   constexpr int NST = ct_nstages(N, EPT);
   if constexpr (S < NST) {
     constexpr int RAD = INV ? ct_radix(N, EPT, NST - 1 - S) : ct_radix(N, EPT, S);
-    fft_stage_ct<R, N, EPT, RAD, NSACC, INV, PADW, SL, NL, T, S == 0, S == NST - 1>(sm, tw, load, store);
-    tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, S + 1, NSACC * RAD>(sm, tw, load, store);
+    fft_stage_ct<R, N, EPT, RAD, NSACC, INV, PADW, SL, NL, T, S == 0, S == NST - 1, LINE_FAST, SA>(sm, tw, load,
+                                                                                                  store);
+    tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, LINE_FAST, SA, S + 1, NSACC * RAD>(sm, tw, load, store);
   }
 }
-// Full transform of the NL lines of the tile; tw[t] = exp(-2 pi i t / N).
+// Full transform of the NL lines of a line-major tile; tw[t] = exp(-2 pi i t / N).
 template <typename R, int N, int EPT, bool INV, int PADW, int SL, int NL, int T, class Load, class Store>
 __device__ __forceinline__ void tile_fft_ct(cx<R> *sm, const cx<R> *__restrict__ tw, Load load, Store store) {
-  tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, 0, 1>(sm, tw, load, store);
+  tile_fft_ct_from<R, N, EPT, INV, PADW, SL, NL, T, false, 1, 0, 1>(sm, tw, load, store);
+}
+// ... of a column tile of NL lines (element a of line l at a NL + l).
+template <typename R, int N, int EPT, bool INV, int NL, int T, class Load, class Store>
+__device__ __forceinline__ void tile_fft_ct_cols(cx<R> *sm, const cx<R> *__restrict__ tw, Load load, Store store) {
+  tile_fft_ct_from<R, N, EPT, INV, 0, 1, NL, T, true, NL, 0, 1>(sm, tw, load, store);
 }
 
 // ------------------------------------------- Crank-Nicolson (Thomas) solve

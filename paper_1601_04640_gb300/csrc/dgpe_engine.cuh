@@ -709,6 +709,26 @@ template <typename R> struct EngineT : Engine {
         if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL>, two))) return r;
         if ((r = smem_attr(k_cn_strided_pipe<R, R, CL, false>, two))) return r;
         if ((r = smem_attr(k_cn_strided_pipe<R, Cx, CL, false>, two))) return r;
+        if constexpr (sizeof(R) == 4 && CL == 16) {
+          r = with_pow2_len(cn[a].n, [&](auto Nc) -> int {
+            constexpr int N = decltype(Nc)::value;
+            if constexpr (N != 0) {
+              int q;
+              if constexpr (16 * (N / 16) <= DGPE_MAXT) {
+                if ((q = smem_attr(k_cn_pipe_ct<R, R, 16, true, N, 16>, two))) return q;
+                if ((q = smem_attr(k_cn_pipe_ct<R, R, 16, false, N, 16>, two))) return q;
+                if ((q = smem_attr(k_cn_pipe_ct<R, Cx, 16, false, N, 16>, two))) return q;
+              }
+              if constexpr (8 * (N / 16) <= DGPE_MAXT) {
+                if ((q = smem_attr(k_cn_pipe_ct<R, R, 16, true, N, 8>, two))) return q;
+                if ((q = smem_attr(k_cn_pipe_ct<R, R, 16, false, N, 8>, two))) return q;
+                if ((q = smem_attr(k_cn_pipe_ct<R, Cx, 16, false, N, 8>, two))) return q;
+              }
+            }
+            return DGPE_OK;
+          });
+          if (r) return r;
+        }
         // persistent grid: as many CTAs as fit on the device, at most one per
         // tile, each double-buffered (the next tile is prefetched)
         const int ntiles = (int)(cn[a].grid.x * cn[a].grid.y);
@@ -741,8 +761,42 @@ template <typename R> struct EngineT : Engine {
     A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = f.W; A.nxh = nx / 2;
     return A;
   }
+  // FP32, power-of-two length, modes 0-2: the length-specialised transform
+  bool launch_fft_ct(const FtCfg &f, int mode, const SArgs<R> &A, cudaStream_t s) {
+    if constexpr (sizeof(R) != 4) {
+      return false;
+    } else {
+      if (mode > 2 || var[f.axis] != VAR_P2 || !(f.W == 16 || f.W == 8 || f.W == 4)) return false;
+      return with_pow2_len(f.n, [&](auto Nc) -> int {
+        constexpr int N = decltype(Nc)::value;
+        if constexpr (N == 0) {
+          return 0;
+        } else {
+          auto go = [&](auto Wc) {
+            constexpr int WW = decltype(Wc)::value;
+            if constexpr (WW * N / EPT_S <= DGPE_MAXT_FFT) {
+              if (mode == 0) k_fft_strided_ct<EPT_S, 0, N, WW><<<f.grid, f.T, f.smem, s>>>(A);
+              else if (mode == 1) k_fft_strided_ct<EPT_S, 1, N, WW><<<f.grid, f.T, f.smem, s>>>(A);
+              else k_fft_strided_ct<EPT_S, 2, N, WW><<<f.grid, f.T, f.smem, s>>>(A);
+              return 1;
+            } else {
+              return 0;
+            }
+          };
+          if (f.W == 16) return go(std::integral_constant<int, 16>{});
+          if (f.W == 8) return go(std::integral_constant<int, 8>{});
+          return go(std::integral_constant<int, 4>{});
+        }
+      }) != 0;
+    }
+  }
   int launch_fft(const FtCfg &f, int mode, cudaStream_t s) {
     SArgs<R> A = sargs(f);
+    if (launch_fft_ct(f, mode, A, s)) {
+      launched(1);
+      DGPE_LCK(__func__);
+      return DGPE_OK;
+    }
     with_svar<EPT_S>(var[f.axis], [&](auto EPc, auto P2c) -> int {
       constexpr int EP = decltype(EPc)::value;
       constexpr bool P2 = decltype(P2c)::value;
@@ -760,6 +814,34 @@ template <typename R> struct EngineT : Engine {
     DGPE_LCK(__func__);
     return DGPE_OK;
   }
+  // FP32, power-of-two length, tile width 16 or 8: the length-specialised
+  // CN pass (same grid, block and shared memory as k_cn_strided_pipe)
+  bool launch_cn_ct(const CnCfg &c, int axis, const CArgs<R> &A, int ncb, int ntiles, cudaStream_t s) {
+    if constexpr (sizeof(R) != 4) {
+      return false;
+    } else {
+      if (var[axis] != VAR_P2 || !(c.W == 16 || c.W == 8)) return false;
+      return with_pow2_len(c.n, [&](auto Nc) -> int {
+        constexpr int N = decltype(Nc)::value;
+        if constexpr (N == 0) {
+          return 0;
+        } else {
+          auto go = [&](auto Wc) {
+            constexpr int WW = decltype(Wc)::value;
+            if constexpr (WW * (N / 16) <= DGPE_MAXT) {
+              if (imag && A.norm) k_cn_pipe_ct<R, R, 16, true, N, WW><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+              else if (imag) k_cn_pipe_ct<R, R, 16, false, N, WW><<<c.pgrid[0], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+              else k_cn_pipe_ct<R, Cx, 16, false, N, WW><<<c.pgrid[1], c.T, 2 * c.smem, s>>>(A, ncb, ntiles);
+              return 1;
+            } else {
+              return 0;
+            }
+          };
+          return (c.W == 16) ? go(std::integral_constant<int, 16>{}) : go(std::integral_constant<int, 8>{});
+        }
+      }) != 0;
+    }
+  }
   int launch_cn(int axis, bool final_pass, cudaStream_t s, Cx *buf = nullptr, bool adjoint = false) {
     if (cn_serial) return launch_lines(axis, final_pass, s, buf, adjoint);
     const CnCfg &c = cn[axis];
@@ -770,6 +852,11 @@ template <typename R> struct EngineT : Engine {
     A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
     A.norm = (final_pass && imag) ? 1 : 0; A.tau = adjoint ? -tau[axis] : tau[axis];
     const int ncb = (int)c.grid.x, ntiles = (int)(c.grid.x * c.grid.y);
+    if (launch_cn_ct(c, axis, A, ncb, ntiles, s)) {
+      launched(1);
+      DGPE_LCK(__func__);
+      return DGPE_OK;
+    }
     with_cl(var[axis], [&](auto CLc) -> int {
       constexpr int CL = decltype(CLc)::value;
       // the norm's code only in the pass that takes the norm

@@ -792,6 +792,46 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_st
   fft_strided_body<R, EPT, MODE, POW2>(A);
 }
 
+// FP32 strided transforms (MODE 0 forward, 1 inverse, 2 forward . U .
+// inverse) with the line length N and tile width W as compile-time constants
+// (power-of-two lengths): the same arithmetic as fft_strided_body, with every
+// index folded (tile_fft_ct_cols).  Twiddles from a shared copy.
+template <int EPT, int MODE, int N, int W>
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_strided_ct(const __grid_constant__ SArgs<float> A) {
+  typedef float R;
+  typedef float2 Cx;
+  constexpr int T = W * N / EPT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Cx *sm = reinterpret_cast<Cx *>(smraw);  // [a][W]
+  __shared__ __align__(16) Cx s_tw[N];
+  for (int i = threadIdx.x; i < N; i += T) s_tw[i] = A.tw[i];
+  __syncthreads();
+  const int c0 = blockIdx.x * W;
+  const size_t base = (size_t)blockIdx.y * A.ostride + c0;
+  const long long es = A.estride;
+  const bool fullw = c0 + W <= A.ncols;
+  Cx *__restrict__ spec = A.spec;
+  auto gload = [&](int l, int a) -> Cx {
+    return (fullw || c0 + l < A.ncols) ? spec[base + a * es + l] : czero<Cx>();
+  };
+  auto gstore = [&](int l, int a, Cx v) {
+    if (fullw || c0 + l < A.ncols) spec[base + a * es + l] = v;
+  };
+  if constexpr (MODE == 0) {
+    tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, gload, gstore);
+  } else if constexpr (MODE == 1) {
+    tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, gload, gstore);
+  } else {
+    auto mstore = [&](int l, int a, Cx v) {
+      const R u = (fullw || c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
+      sm[a * W + l] = cscale(v, u);
+    };
+    tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, gload, mstore);
+    auto sload = [&](int l, int a) -> Cx { return sm[a * W + l]; };
+    tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, gstore);
+  }
+}
+
 // ------------------------------------------------------- P2 / P3 (strided)
 // NORM false: a pass without the norm (no |x|^2 code at all); true: the
 // runtime flag A.norm decides.
@@ -945,6 +985,99 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
 #pragma unroll
       for (int i = 0; i < CL; ++i) {
         const int a = r0 + i * A.TPL;
+        const cx<R> v = tb[lc * P + a + a / CL];
+        dst[(size_t)a * es] = v;
+        if (NORM && A.norm) ts += v.x * v.x + v.y * v.y;
+      }
+      if (NORM && A.norm) acc += (double)ts;
+    }
+    __syncthreads();  // the buffer is refilled two iterations later
+  }
+  cp_async_wait<0>();
+  if (!A.final_pass) return;
+  const unsigned nblk = gridDim.x;
+  if (NORM && A.norm) {
+    double sblk = block_sum(acc, red);
+    if (threadIdx.x == 0) A.partial[blockIdx.x] = sblk;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned ticket = atomicAdd(A.counter, 1u);
+    am_last = (ticket == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (NORM && A.norm) {
+    double sum = 0.0;
+    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) sum += __ldcg(A.partial + i);
+    sum = block_sum(sum, red);
+    if (threadIdx.x == 0) {
+      const double norm = A.prm[PRM_CELL] * sum;
+      if (norm > 0.0 && isfinite(norm)) A.prm[PRM_SC] = 1.0 / sqrt(norm);
+      else A.prm[PRM_NONFINITE] = 1.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    *A.step += 1;
+    *A.counter = 0u;
+  }
+}
+
+// The same pass with the line length N and tile width W as compile-time
+// constants (FP32, power-of-two lengths): every index folds.
+template <typename R, typename Coef, int CL, bool NORM, int N, int W>
+__global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_pipe_ct(const __grid_constant__ CArgs<R> A, int ncb, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  __shared__ int am_last;
+  constexpr int n = N, TPL = N / CL, P = N + N / CL + 1, lW = ct_log2(W);
+  static_assert(W * TPL <= DGPE_MAXT, "block size");
+  cx<R> *const buf0 = reinterpret_cast<cx<R> *>(smraw);  // buffer k at buf0 + k W P
+  const long long es = A.estride;
+  const int lc = threadIdx.x & (W - 1), r0 = threadIdx.x >> lW;
+  auto fetch = [&](int tile, cx<R> *tb) {
+    const int cb = tile % ncb, o = tile / ncb;
+    const int c0 = cb * W;
+    if (c0 + lc < A.ncols) {
+      const cx<R> *src = A.psi + (size_t)o * A.ostride + c0 + lc;
+#pragma unroll
+      for (int i = 0; i < CL; ++i) {
+        const int a = r0 + i * TPL;
+        cp_async_elem(tb + lc * P + a + a / CL, src + (size_t)a * es);
+      }
+    }
+    cp_async_commit();
+  };
+  constexpr bool TAB = (sizeof(R) == 8);
+  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * P];
+  if (!TAB) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), n);  // visible after the loop's first barrier
+  double acc = 0.0;
+  int k = 0;
+  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, buf0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) fetch(next, buf0 + (k ^ 1) * W * P);
+    else cp_async_commit();  // keep one group per iteration
+    cp_async_wait<1>();      // this tile's copies are done (the next may be in flight)
+    __syncthreads();
+    const int cb = tile % ncb, o = tile / ncb;
+    const int c0 = cb * W;
+    cx<R> *tb = buf0 + k * W * P;
+    const int l = threadIdx.x / TPL, q = threadIdx.x - l * TPL;
+    if constexpr (TAB) cn_line<R, Coef, CL>(tb + l * P, n, TPL, q, make_kt<Coef>(A.tau),
+                                        reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
+    else cn_line_st<R, Coef, CL>(tb + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
+    __syncthreads();
+    if (c0 + lc < A.ncols) {
+      cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;
+      // |x|^2 of the thread's CL sites summed in R (FP32: an FP64 sum per
+      // site held the FP32 final pass at the FP64 pipe's rate, 0.21 against
+      // 0.08 ms at 256^3), then accumulated in FP64 across tiles and blocks
+      R ts = (R)0;
+#pragma unroll
+      for (int i = 0; i < CL; ++i) {
+        const int a = r0 + i * TPL;
         const cx<R> v = tb[lc * P + a + a / CL];
         dst[(size_t)a * es] = v;
         if (NORM && A.norm) ts += v.x * v.x + v.y * v.y;
