@@ -40,7 +40,7 @@ WORKLOADS = {
     "batched2d": dict(n=None, desc="batched 2D: 512 independent XY problems, square grids from "
                       "{64,96,128,160,256,384,512}^2, h=0.2, nu_y in [0.5,2], g in [10,200], g_dd/g in "
                       "[0,0.8], quasi-2D kernel d=0.5, half imaginary / half real time, dt=1e-3, "
-                      "FP32-bulk, one graph launch per step (seed 4640)"),
+                      "FP32-bulk, one persistent kernel launch per call (seed 4640)"),
     "adjoint": dict(n=(128, 128, 128), h=(0.15, 0.15, 0.15), nu=(1.0, 1.0, 0.5), g=200.0, gdd=60.0,
                     dt=1e-3, widths=(1.0, 1.0, 0.5), seed=160104640, g_prep=None, prep_steps=0,
                     desc="adjoint real3d 128^3, h=0.15, FP32-bulk, dt=1e-3, 1000 steps, V(t)=V0(1+sum "
@@ -592,7 +592,7 @@ def _peak_line(metric, value, unit, steps, warmup, ms, dtype, cfg, world, **extr
 
 
 def bench_batched(args, wl, world, rank, local):
-    """512 independent 2D problems stepped by one graph launch per step.  With
+    """512 independent 2D problems stepped by one persistent kernel launch.  With
     N ranks the sweep is partitioned by cost (shard.partition): each rank steps
     its share, the only exchange is a host-side gather of the results."""
     import torch
@@ -656,6 +656,21 @@ def bench_batched(args, wl, world, rank, local):
         mus[i] = B.observables(j)["mu"]
     obs0 = B.observables(0)
     B.close()
+    # comparison: the same sweep as per-size-class batched kernels in one graph
+    Bc = dgpe.Batch(probs, stream=stream.cuda_stream, classes=True)
+    for i, st in enumerate(states):
+        Bc.set_psi(i, st)
+    Bc.step(args.warmup)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    Bc.step(args.steps)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    per_class = {"ms_per_step": shard.max_over_ranks(c0.elapsed_time(c1)) / args.steps,
+                 "launches_per_step": Bc.info()["launches_per_step"]}
+    Bc.close()
     mus = shard.gather(mus)
     if rank != 0:
         return
@@ -691,8 +706,9 @@ def bench_batched(args, wl, world, rank, local):
                                 "traffic": None, "algorithmic_bytes_per_step": info["bytes_per_step"]},
                       e2e={"value": sweep_sites * ke / te, "unit": "site-updates/s",
                            "h2d_bytes_per_step": 16 * sweep_sites, "d2h_bytes_per_step": 16 * sweep_sites},
-                      gpu_launches=info["launches_per_step"] * args.steps, clocks=clocks, cpu_baseline=cpu,
-                      create_s=t_create, observables_problem0={"mu": obs0["mu"], "norm": obs0["norm"]})
+                      gpu_launches=info["launches_per_step"], clocks=clocks, cpu_baseline=cpu,
+                      create_s=t_create, observables_problem0={"mu": obs0["mu"], "norm": obs0["norm"]},
+                      per_class_graph=per_class)
     print(json.dumps(line))
 
 

@@ -119,6 +119,13 @@ extern "C" {
                                    persistent CTAs fed by bulk asynchronous
                                    copies (same arithmetic) */
 
+#define DGPE_FLAG_BATCH_CLASSES 64u /* batched form (set on any problem): step
+                                   the batch as per-size-class batched kernels
+                                   (4 per class) in one captured graph whose
+                                   class branches run concurrently, instead of
+                                   the persistent work-list kernel (same
+                                   arithmetic; no bounded waits) */
+
 typedef struct dgpe_params {
   int dim;          /* 2 or 3 */
   int plane;        /* DGPE_PLANE_* (2D) */
@@ -257,21 +264,33 @@ int dgpe_fidelity_gradient(dgpe_t h, const double *psi0, const double *target, i
  * (the paper's imag2dXY / real2dXY programs, one problem each; here a
  * parameter sweep).  ps[0..count-1]: dim 2, plane XY, square grids
  * (nx == ny, any supported length), precision DGPE_FP32_BULK, kernel
- * QUASI2D_XY, imaginary or real time each.  Problems of equal size and mode
- * form a class; each class runs the four 2D passes as batched kernels (one
- * problem per grid z-index) with a tile schedule chosen at create time by
- * timing candidates; one step of all classes is one captured CUDA graph.
- * States start at zero; problem i is addressed by its index. */
+ * QUASI2D_XY, imaginary or real time each.  dgpe_batch_step(b, n) is one
+ * launch of a persistent kernel that advances every problem n steps: its
+ * CTAs take (problem, pass, tile) items from a device work list in ticket
+ * order, each item waiting until its problem's earlier passes are complete
+ * (per-problem counters; every wait is bounded and a wait that runs out makes
+ * the next dgpe_batch_sync / get_psi / observables return DGPE_ETIMEOUT);
+ * 64 x 64 problems stay in one CTA's shared memory for all n steps.  At create
+ * time an autotuner times the orders of the FFT radices for each size and
+ * mode.  States start at zero; problem i is addressed by its index. */
 typedef struct dgpe_batch *dgpe_batch_t;
 int dgpe_batch_create(const dgpe_params *ps, int count, void *cuda_stream, dgpe_batch_t *out);
 void dgpe_batch_destroy(dgpe_batch_t b);
 int dgpe_batch_set_psi(dgpe_batch_t b, int i, const double *psi, size_t n_sites);
 int dgpe_batch_get_psi(dgpe_batch_t b, int i, double *psi, size_t n_sites);   /* synchronises */
-int dgpe_batch_step(dgpe_batch_t b, int n);                                    /* n graph replays */
+int dgpe_batch_step(dgpe_batch_t b, int n);                                    /* one launch, n steps; asynchronous */
+/* Wait for the batch's work; DGPE_ETIMEOUT if a bounded wait ran out. */
+int dgpe_batch_sync(dgpe_batch_t b);
+/* Test hooks of the bounded waits: hold problem i (-1: none) so that its
+ * tiles never count as complete -- every wait on it runs out and the step
+ * returns early with DGPE_ETIMEOUT at the next sync; and the number of polls
+ * (about 64 ns apart) after which a wait gives up (default 4194304). */
+int dgpe_batch_hold_problem(dgpe_batch_t b, int i);
+int dgpe_batch_set_wait_limit(dgpe_batch_t b, long long polls);
 int dgpe_batch_observables(dgpe_batch_t b, int i, dgpe_obs *o);                /* synchronises */
 /* number of classes, total sites, algorithmic HBM bytes of one step */
 int dgpe_batch_info(dgpe_batch_t b, int *classes, long long *sites, double *bytes_per_step);
-int dgpe_batch_launches_per_step(dgpe_batch_t b);
+int dgpe_batch_launches_per_step(dgpe_batch_t b);  /* kernel launches per dgpe_batch_step call: 1 */
 const char *dgpe_batch_last_error(dgpe_batch_t b);
 
 /* Phi_d of |psi|^2 for a caller's state, computed without allocating any

@@ -229,16 +229,27 @@ template <typename T> __device__ __forceinline__ const T &block_args(const T *__
   return dst;
 }
 
+// Shared scratch of a pass body: the bytes a body would otherwise declare as
+// static __shared__ arrays.  A body called with SCR = 0 takes its own size;
+// a kernel that runs several bodies passes one common size to all of them, so
+// they use the same allocation (function-scope __shared__ storage is one
+// object per template instantiation and kernel).
+template <int BYTES> __device__ __forceinline__ unsigned char *shared_scratch() {
+  __shared__ __align__(32) unsigned char buf[BYTES];
+  return buf;
+}
+__host__ __device__ constexpr int scr_align(int b) { return (b + 31) & ~31; }
+
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in;
 // SRC 2: sc^2 psi^2 of a real state (A.psi holds nx reals per row).
 // FMA: twiddled stages in FMA form (tile_fft), roots from A.twf.
-template <typename R, int EPT, int SRC, bool POW2, bool FMA = false>
-__device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
+template <typename R, int EPT, int SRC, bool POW2, bool FMA = false, int SCR = 0>
+__device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
   constexpr int PW = Pad<R>::W;
   const int n = A.nx, SL = A.pitchz, nrows = A.nrows;
-  const int p0 = blockIdx.x * A.LP;
+  const int p0 = bx * A.LP;
   const R sc = (R)A.prm[PRM_SC];
   const R sc2 = sc * sc;
   const cx<R> *__restrict__ psi = A.psi;
@@ -259,8 +270,12 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
     return mk<R>(d0, d1);
   };
   auto store = [&](int l, int a, cx<R> v) { zt[sidx<PW>(l, a, SL, 1)] = v; };
-  __shared__ __align__(16) cx<R> s_tw[(DGPE_TW_SMEM && !FMA) ? 512 : 1];
-  __shared__ __align__(16) rt4<R> s_rt[FMA ? 512 : 1];
+  constexpr int NTW = (DGPE_TW_SMEM && !FMA) ? 512 : 1, NRT = FMA ? 512 : 1;
+  constexpr int OFF_RT = scr_align(sizeof(cx<R>) * NTW), NEED = OFF_RT + sizeof(rt4<R>) * NRT;
+  static_assert(SCR == 0 || NEED <= SCR, "shared scratch too small");
+  unsigned char *scr = shared_scratch<SCR ? SCR : NEED>();
+  cx<R> *s_tw = reinterpret_cast<cx<R> *>(scr);
+  rt4<R> *s_rt = reinterpret_cast<rt4<R> *>(scr + OFF_RT);
   const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, n);
   const rt4<R> *rt = FMA ? stage_roots(s_rt, A.twf, n) : nullptr;
   tile_fft<R, EPT, false, false, PW, POW2, FMA>(zt, SL, 1, A.LP, A.pl, tw, load, store, rt);
@@ -280,7 +295,7 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A) {
 }
 template <typename R, int EPT, int SRC = 0, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x(const __grid_constant__ XArgs<R> A) {
-  dens_r2c_x_body<R, EPT, SRC, POW2, FMA>(A);
+  dens_r2c_x_body<R, EPT, SRC, POW2, FMA>(A, blockIdx.x);
 }
 // batched: one problem per blockIdx.z
 template <typename R, int EPT, bool POW2>
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
   __shared__ XArgs<R> sA;
   const XArgs<R> &A = block_args(args, sA);
   if (blockIdx.x * A.LP * 2 >= (unsigned)A.nrows) return;
-  dens_r2c_x_body<R, EPT, 0, POW2>(A);
+  dens_r2c_x_body<R, EPT, 0, POW2>(A, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ P1
@@ -300,19 +315,29 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
 //   imaginary parts: the exponential scales each part by its own row's
 //   factor, and one Crank-Nicolson solve with the real coefficients of
 //   imaginary time advances both rows.
-template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false>
-__device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false, int SCR = 0>
+__device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
   cx<R> *zt = pt + 2 * A.LP * A.pitch;           // Z tile: LP lines, pitch pitchz
   constexpr int PW = Pad<R>::W;
-  __shared__ R s_k[4];  // dt s(t) f, g dt f, g_dd dt f, sc (thread 0, from FP64)
-  __shared__ R s_vyz[DGPE_MAXT];  // V_y + V_z of the CTA's rows (2 LP <= DGPE_MAXT)
   constexpr bool TAB = (sizeof(R) == 8);
-  __shared__ R s_dvx[TAB ? 512 : 1];  // FP64 real time: dt s(t) V_x
-  // FP32: padded shared copy of the four CN tables (FP64 reads them from
-  // global memory: its FP64 pipe, not the table loads, is the limit)
-  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
+  // shared scratch: s_k[4] (dt s(t) f, g dt f, g_dd dt f, sc; thread 0, from
+  // FP64), s_vyz[DGPE_MAXT] (V_y + V_z of the CTA's rows, 2 LP <= DGPE_MAXT),
+  // s_dvx (FP64 real time: dt s(t) V_x), s_tab (FP32: padded shared copy of
+  // the four CN tables; FP64 reads them from global memory: its FP64 pipe,
+  // not the table loads, is the limit), s_rt (FMA-form roots)
+  constexpr int NDVX = TAB ? 512 : 1, NTAB = TAB ? 1 : 4 * (512 + 512 / CL + 1);
+  constexpr int NRT = (FMA && MODE != 2) ? 512 : 1;
+  constexpr int OFF_VYZ = scr_align(sizeof(R) * 4), OFF_DVX = OFF_VYZ + scr_align(sizeof(R) * DGPE_MAXT);
+  constexpr int OFF_TAB = OFF_DVX + scr_align(sizeof(R) * NDVX), OFF_RT = OFF_TAB + scr_align(sizeof(Coef) * NTAB);
+  constexpr int NEED = OFF_RT + sizeof(rt4<R>) * NRT;
+  static_assert(SCR == 0 || NEED <= SCR, "shared scratch too small");
+  unsigned char *scr = shared_scratch<SCR ? SCR : NEED>();
+  R *const s_k = reinterpret_cast<R *>(scr);
+  R *const s_vyz = reinterpret_cast<R *>(scr + OFF_VYZ);
+  R *const s_dvx = reinterpret_cast<R *>(scr + OFF_DVX);
+  Coef *const s_tab = reinterpret_cast<Coef *>(scr + OFF_TAB);
   if (!TAB && MODE != 1 && MODE != 3) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), A.nx);
   constexpr bool RS = (MODE == 4);  // real state
   R *const ptr = reinterpret_cast<R *>(pt);
@@ -320,7 +345,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   auto rs_at = [&](int L, int a) -> R & { return ptr[2 * ((L >> 1) * A.pitch + a + a / CL) + (L & 1)]; };
   const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
   const int ln = POW2 ? ilog2(n) : 0;
-  const int p0 = blockIdx.x * A.LP;
+  const int p0 = bx * A.LP;
   const int T = blockDim.x, t = threadIdx.x;
   auto row_of = [&](int idx) { return POW2 ? (idx >> ln) : (idx / n); };
   auto col_of = [&](int idx) { return POW2 ? (idx & (n - 1)) : (idx % n); };
@@ -336,7 +361,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
   // for this pass; the FP32 block's shared memory is sized for 3 blocks/SM);
   // the FMA-form roots (FP64) from a shared copy
   const cx<R> *s_twp = A.tw;
-  __shared__ __align__(16) rt4<R> s_rt[(FMA && MODE != 2) ? 512 : 1];
+  rt4<R> *const s_rt = reinterpret_cast<rt4<R> *>(scr + OFF_RT);
   const rt4<R> *rt = nullptr;
   if constexpr (FMA && MODE != 2) rt = stage_roots(s_rt, A.twi, n);
   if constexpr (RS) {
@@ -484,13 +509,13 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A) {
 }
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx(const __grid_constant__ XArgs<R> A) {
-  c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2, FMA>(A);
+  c2r_x_exp_cnx_body<R, Coef, EPT, CL, MODE, POW2, FMA>(A, blockIdx.x);
 }
 template <typename R, typename Coef, int EPT, int CL, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P1(R)) k_c2r_x_exp_cnx_batch(const XArgs<R> *__restrict__ args) {
   __shared__ XArgs<R> sA;
   const XArgs<R> &A = block_args(args, sA);
-  c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A);
+  c2r_x_exp_cnx_body<R, Coef, EPT, CL, 0, POW2>(A, blockIdx.x);
 }
 
 #ifndef DGPE_WAIT_LIMIT
@@ -730,23 +755,30 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
 // ------------------------------------------------- P5 / P6 / P7 (strided)
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
-template <typename R, int EPT, int MODE, bool POW2, bool FMA = false>
-__device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
+template <typename R, int EPT, int MODE, bool POW2, bool FMA = false, int SCR = 0>
+__device__ __forceinline__ void fft_strided_body(const SArgs<R> &A, int bx, int by, int gx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
-  __shared__ double red[32];
-  __shared__ __align__(16) cx<R> s_tw[(DGPE_TW_SMEM && !FMA) ? 512 : 1];
-  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, A.n);
   // FMA-form roots: forward (modes 0, 2, 3) and inverse (modes 1, 2)
   constexpr bool NF = FMA && MODE != 1, NI = FMA && (MODE == 1 || MODE == 2);
-  __shared__ __align__(16) rt4<R> s_rf[NF ? 512 : 1];
-  __shared__ __align__(16) rt4<R> s_ri[NI ? 512 : 1];
+  // shared scratch: red[32], twiddles, forward and inverse FMA-form roots
+  constexpr int NTW = (DGPE_TW_SMEM && !FMA) ? 512 : 1;
+  constexpr int OFF_TW = scr_align(sizeof(double) * 32), OFF_RF = OFF_TW + scr_align(sizeof(cx<R>) * NTW);
+  constexpr int OFF_RI = OFF_RF + scr_align(sizeof(rt4<R>) * (NF ? 512 : 1));
+  constexpr int NEED = OFF_RI + sizeof(rt4<R>) * (NI ? 512 : 1);
+  static_assert(SCR == 0 || NEED <= SCR, "shared scratch too small");
+  unsigned char *scr = shared_scratch<SCR ? SCR : NEED>();
+  double *const red = reinterpret_cast<double *>(scr);
+  cx<R> *const s_tw = reinterpret_cast<cx<R> *>(scr + OFF_TW);
+  rt4<R> *const s_rf = reinterpret_cast<rt4<R> *>(scr + OFF_RF);
+  rt4<R> *const s_ri = reinterpret_cast<rt4<R> *>(scr + OFF_RI);
+  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, A.n);
   const rt4<R> *rf = nullptr, *ri = nullptr;
   if constexpr (NF) rf = stage_roots(s_rf, A.twf, A.n);
   if constexpr (NI) ri = stage_roots(s_ri, A.twi, A.n);
   const int W = A.W;
-  const int c0 = blockIdx.x * W;
-  const size_t base = (size_t)blockIdx.y * A.ostride + c0;
+  const int c0 = bx * W;
+  const size_t base = (size_t)by * A.ostride + c0;
   const long long es = A.estride;
   cx<R> *__restrict__ spec = A.spec;
   auto gload = [&](int l, int a) -> cx<R> {
@@ -778,18 +810,18 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A) {
     };
     tile_fft<R, EPT, false, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, astore, rf);
     double s = block_sum(acc, red);
-    if (threadIdx.x == 0) A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x == 0) A.partial[(size_t)by * gx + bx] = s;
   }
 }
 template <typename R, int EPT, int MODE, bool POW2 = true, bool FMA = false>
 __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided(const __grid_constant__ SArgs<R> A) {
-  fft_strided_body<R, EPT, MODE, POW2, FMA>(A);
+  fft_strided_body<R, EPT, MODE, POW2, FMA>(A, blockIdx.x, blockIdx.y, gridDim.x);
 }
 template <typename R, int EPT, int MODE, bool POW2>
 __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT(R, EPT)) k_fft_strided_batch(const SArgs<R> *__restrict__ args) {
   __shared__ SArgs<R> sA;
   const SArgs<R> &A = block_args(args, sA);
-  fft_strided_body<R, EPT, MODE, POW2>(A);
+  fft_strided_body<R, EPT, MODE, POW2>(A, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // FP32 strided transforms (MODE 0 forward, 1 inverse, 2 forward . U .
@@ -835,16 +867,23 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_stride
 // ------------------------------------------------------- P2 / P3 (strided)
 // NORM false: a pass without the norm (no |x|^2 code at all); true: the
 // runtime flag A.norm decides.
-template <typename R, typename Coef, int CL, bool NORM = true>
-__device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
+template <typename R, typename Coef, int CL, bool NORM = true, int SCR = 0>
+__device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int by, int gx, int gy) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *tile = reinterpret_cast<cx<R> *>(smraw);  // [W][pitch]
-  __shared__ double red[32];
-  __shared__ int am_last;
+  constexpr bool TAB = (sizeof(R) == 8);
+  // shared scratch: red[32], am_last, s_tab (FP32: padded copy of the tables)
+  constexpr int OFF_LAST = scr_align(sizeof(double) * 32), OFF_TAB = OFF_LAST + 32;
+  constexpr int NEED = OFF_TAB + sizeof(Coef) * (TAB ? 1 : 4 * (512 + 512 / CL + 1));
+  static_assert(SCR == 0 || NEED <= SCR, "shared scratch too small");
+  unsigned char *scr = shared_scratch<SCR ? SCR : NEED>();
+  double *const red = reinterpret_cast<double *>(scr);
+  int &am_last = *reinterpret_cast<int *>(scr + OFF_LAST);
+  Coef *const s_tab = reinterpret_cast<Coef *>(scr + OFF_TAB);
   const int W = A.W, n = A.n, P = A.pitch;
   const int lW = ilog2(W);
-  const int c0 = blockIdx.x * W;
-  const size_t base = (size_t)blockIdx.y * A.ostride + c0;
+  const int c0 = bx * W;
+  const size_t base = (size_t)by * A.ostride + c0;
   const long long es = A.estride;
   // thread t owns column t % W and rows t / W + i TPL, i < CL (blockDim =
   // W TPL, n = CL TPL): all CL loads are in flight before the first
@@ -862,8 +901,6 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
     }
   }
   __syncthreads();
-  constexpr bool TAB = (sizeof(R) == 8);
-  __shared__ __align__(16) Coef s_tab[TAB ? 1 : 4 * (512 + 512 / CL + 1)];
   if (!TAB) {
     stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), n);
     __syncthreads();
@@ -889,8 +926,8 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
   // Last pass of the step: norm partials (imaginary time) and, in the last
   // block to finish, the deterministic FP64 total, the new scale and the
   // step counter.
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned nblk = (unsigned)(gx * gy);
+  const unsigned bid = (unsigned)(by * gx + bx);
   if (A.norm) {
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) A.partial[bid] = s;
@@ -920,13 +957,13 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A) {
 }
 template <typename R, typename Coef, int CL, bool NORM = true>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided(const __grid_constant__ CArgs<R> A) {
-  cn_strided_body<R, Coef, CL, NORM>(A);
+  cn_strided_body<R, Coef, CL, NORM>(A, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 template <typename R, typename Coef, int CL, bool NORM = true>
 __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB(R)) k_cn_strided_batch(const CArgs<R> *__restrict__ args) {
   __shared__ CArgs<R> sA;
   const CArgs<R> &A = block_args(args, sA);
-  cn_strided_body<R, Coef, CL, NORM>(A);
+  cn_strided_body<R, Coef, CL, NORM>(A, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 // Persistent, double-buffered CN pass: each CTA walks tiles

@@ -39,6 +39,7 @@ DGPE_FLAG_CN_CHUNKED = 4
 DGPE_FLAG_STRANG = 8
 DGPE_FLAG_REAL_PSI = 16
 DGPE_FLAG_P1_ONESHOT = 32
+DGPE_FLAG_BATCH_CLASSES = 64
 
 EXPORTS = [
     "dgpe_create", "dgpe_destroy", "dgpe_set_psi", "dgpe_get_psi", "dgpe_set_psi_device",
@@ -50,7 +51,7 @@ EXPORTS = [
     "dgpe_step_adjoint", "dgpe_fidelity_gradient",
     "dgpe_batch_create", "dgpe_batch_destroy", "dgpe_batch_set_psi", "dgpe_batch_get_psi",
     "dgpe_batch_step", "dgpe_batch_observables", "dgpe_batch_info", "dgpe_batch_launches_per_step",
-    "dgpe_batch_last_error",
+    "dgpe_batch_last_error", "dgpe_batch_sync", "dgpe_batch_hold_problem", "dgpe_batch_set_wait_limit",
 ]
 
 
@@ -392,9 +393,11 @@ def dgpe_fidelity_gradient(h, psi0, target, nsteps: int, every: int, M: int = 0)
 class Batch:
     """Many independent 2D XY problems (FP32-bulk) stepped by one graph launch.
 
-    problems: list of dicts with keys n (nx, ny), h, nu, g, gdd, dt, imag, qd."""
+    problems: list of dicts with keys n (nx, ny), h, nu, g, gdd, dt, imag, qd.
+    classes: step with per-size-class batched kernels in one graph (the
+    comparison form) instead of the persistent work-list kernel."""
 
-    def __init__(self, problems, stream: int = 0):
+    def __init__(self, problems, stream: int = 0, classes: bool = False):
         lib = load()
         if not getattr(lib, "_batch_bound", False):
             lib.dgpe_batch_create.argtypes = [C.POINTER(dgpe_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
@@ -409,6 +412,9 @@ class Batch:
             lib.dgpe_batch_launches_per_step.argtypes = [C.c_void_p]
             lib.dgpe_batch_last_error.argtypes = [C.c_void_p]
             lib.dgpe_batch_last_error.restype = C.c_char_p
+            lib.dgpe_batch_sync.argtypes = [C.c_void_p]
+            lib.dgpe_batch_hold_problem.argtypes = [C.c_void_p, C.c_int]
+            lib.dgpe_batch_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
             lib._batch_bound = True
         self.lib = lib
         arr = (dgpe_params * len(problems))()
@@ -416,7 +422,8 @@ class Batch:
         for i, q in enumerate(problems):
             arr[i] = make_params(2, q["n"], q["h"], q["nu"], q["g"], q["gdd"], q["dt"], q["imag"], False,
                                  DGPE_KERNEL_QUASI2D_XY, q.get("qd", 0.5), split=q.get("split", "lie"),
-                                 real_psi=q.get("real_psi", False))
+                                 real_psi=q.get("real_psi", False),
+                                 flags=DGPE_FLAG_BATCH_CLASSES if classes else 0)
             self.shapes.append((q["n"][1], q["n"][0]))
         self.h = C.c_void_p()
         rc = lib.dgpe_batch_create(arr, len(problems), C.c_void_p(stream), C.byref(self.h))
@@ -438,6 +445,16 @@ class Batch:
 
     def step(self, n=1):
         self._chk(self.lib.dgpe_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._chk(self.lib.dgpe_batch_sync(self.h))
+
+    def hold_problem(self, i):
+        """Test hook: problem i's tiles never complete (-1 releases)."""
+        self._chk(self.lib.dgpe_batch_hold_problem(self.h, int(i)))
+
+    def set_wait_limit(self, polls):
+        self._chk(self.lib.dgpe_batch_set_wait_limit(self.h, int(polls)))
 
     def observables(self, i):
         o = dgpe_obs()

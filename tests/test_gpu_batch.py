@@ -111,3 +111,63 @@ def test_batch_rejects_bad_problems():
     q = dict(n=(64, 32), h=(0.2, 0.2), nu=(1.0, 1.0), g=10.0, gdd=1.0, dt=1e-3, imag=True, qd=0.5)
     with pytest.raises(dgpe.DgpeError):
         dgpe.Batch([q])
+
+
+def test_batch_bounded_wait_runs_out_and_recovers():
+    """The persistent step's waits are bounded: with one problem held (its
+    tiles never count as complete, a test hook) every wait on it runs out, the
+    kernel finishes, and the next sync reports DGPE_ETIMEOUT.  Released, the
+    same batch steps correctly again (against the single solver)."""
+    gbuild.build()
+    probs = synth.batched_problems(4640, 4, sizes=synth.BATCH_SIZES)
+    for i, n in enumerate((64, 128, 160, 96)):
+        probs[i]["n"] = (n, n)
+    with dgpe.Batch(probs) as B:
+        assert B.info()["launches_per_step"] == 1
+        for i, q in enumerate(probs):
+            B.set_psi(i, _psi0(q))
+        for held in (1, 0):  # a tile-list problem, then the shared-memory-resident one
+            B.set_wait_limit(2000)
+            B.hold_problem(held)
+            B.step(2)
+            with pytest.raises(dgpe.DgpeError) as e:
+                B.sync()
+            assert e.value.code == dgpe.DGPE_ETIMEOUT
+            B.hold_problem(-1)
+        B.set_wait_limit(1 << 22)
+        for i, q in enumerate(probs):
+            B.set_psi(i, _psi0(q))
+        B.step(5)
+        B.sync()
+        outs = [B.get_psi(i) for i in range(len(probs))]
+    for i, q in enumerate(probs):
+        with dgpe.Solver(2, q["n"], q["h"], q["nu"], q["g"], q["gdd"], q["dt"], q["imag"], False,
+                         qd=q["qd"]) as s:
+            s.set_psi(_psi0(q))
+            s.step(5)
+            single = s.get_psi()
+        d = np.linalg.norm(outs[i] - single) / np.linalg.norm(single)
+        print(i, q["n"], "batch vs single", d)
+        assert d <= 1e-6
+
+
+def test_batch_per_class_form_matches_persistent():
+    """DGPE_FLAG_BATCH_CLASSES (per-class batched kernels in one graph) and the
+    default persistent work-list kernel step the same problems alike."""
+    gbuild.build()
+    probs = synth.batched_problems(4640, 7, sizes=synth.BATCH_SIZES)
+    for i, n in enumerate(synth.BATCH_SIZES):
+        probs[i]["n"] = (n, n)
+    outs = []
+    for classes in (False, True):
+        with dgpe.Batch(probs, classes=classes) as B:
+            assert B.info()["launches_per_step"] == (4 * B.info()["classes"] if classes else 1)
+            for i, q in enumerate(probs):
+                B.set_psi(i, _psi0(q))
+            B.step(6)
+            B.sync()
+            outs.append([B.get_psi(i) for i in range(len(probs))])
+    for i in range(len(probs)):
+        d = np.linalg.norm(outs[0][i] - outs[1][i]) / np.linalg.norm(outs[1][i])
+        print(i, probs[i]["n"], "persistent vs per-class", d)
+        assert d <= 1e-6
