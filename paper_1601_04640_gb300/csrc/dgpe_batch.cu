@@ -303,6 +303,25 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2)
       if (level == 4) {
         if (B.imag) resident64_run<float>(B, nsteps);
         else resident64_run<float2>(B, nsteps);
+      } else if (B.var == VAR_P2 && (B.n == 128 || B.n == 256 || B.n == 512)) {
+        // power-of-two sides: bodies with the length and tile as constants
+        auto run = [&](auto Nc) {
+          constexpr int N = decltype(Nc)::value, WS = DGPE_MAXT * 16 / N, WCN = DGPE_MAXT / (N / 16);
+          switch (level) {
+            case 0: dens_r2c_x_body<float, 8, 0, true, false, kBatchScr, N>(B.X, tile); break;
+            case 1: fft_strided_body<float, 16, 2, true, false, kBatchScr, N, WS>(B.S, tile, 0, B.tiles[1]); break;
+            case 2:
+              if (B.imag) c2r_x_exp_cnx_body<float, float, 8, 16, 0, true, false, kBatchScr, N>(B.X, tile);
+              else c2r_x_exp_cnx_body<float, float2, 8, 16, 0, true, false, kBatchScr, N>(B.X, tile);
+              break;
+            default:
+              if (B.imag) cn_strided_body<float, float, 16, true, kBatchScr, N, WCN>(B.C, tile, 0, B.tiles[3], 1);
+              else cn_strided_body<float, float2, 16, false, kBatchScr, N, WCN>(B.C, tile, 0, B.tiles[3], 1);
+          }
+        };
+        if (B.n == 128) run(std::integral_constant<int, 128>{});
+        else if (B.n == 256) run(std::integral_constant<int, 256>{});
+        else run(std::integral_constant<int, 512>{});
       } else if (B.var == VAR_P2) {
         switch (level) {
           case 0: dens_r2c_x_body<float, 8, 0, true, false, kBatchScr>(B.X, tile); break;

@@ -159,6 +159,9 @@ inline double wavenumber(int j, int n, double h) {
     }                                                                        \
   } while (0)
 
+#ifndef DGPE_EPT_S_F64
+#define DGPE_EPT_S_F64 8  // FP64 strided transforms: elements per thread (power-of-two lengths)
+#endif
 #ifndef DGPE_FFT_FMA_F32
 #define DGPE_FFT_FMA_F32 0  // FP32 density and strided transforms in FMA form too (measured 3 % slower)
 #endif
@@ -177,7 +180,7 @@ template <class F> int with_pow2_len(int n, F &&f) {
 
 template <typename R> struct EngineT : Engine {
   typedef cx<R> Cx;
-  static constexpr int EPT_S = sizeof(R) == 8 ? 8 : 16;  // strided FFTs, power-of-two lengths
+  static constexpr int EPT_S = sizeof(R) == 8 ? DGPE_EPT_S_F64 : 16;  // strided FFTs, power-of-two lengths
   int var[3] = {VAR_P2, VAR_P2, VAR_P2};           // kernel variant per axis
   static constexpr int PW = 128 / (int)sizeof(Cx); // pad period of line-major tiles
   static constexpr int W = 128 / (int)sizeof(Cx);  // columns per strided tile (128 B)

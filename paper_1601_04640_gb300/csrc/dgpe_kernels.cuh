@@ -243,13 +243,18 @@ __host__ __device__ constexpr int scr_align(int b) { return (b + 31) & ~31; }
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in;
 // SRC 2: sc^2 psi^2 of a real state (A.psi holds nx reals per row).
 // FMA: twiddled stages in FMA form (tile_fft), roots from A.twf.
-template <typename R, int EPT, int SRC, bool POW2, bool FMA = false, int SCR = 0>
+// NC > 0 (FP32, power-of-two nx = NC, the default tile of 2 LP rows and
+// DGPE_MAXT threads): the line length, tile and plan are compile-time
+// constants and the transform is tile_fft_ct.
+template <typename R, int EPT, int SRC, bool POW2, bool FMA = false, int SCR = 0, int NC = 0>
 __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
   constexpr int PW = Pad<R>::W;
-  const int n = A.nx, SL = A.pitchz, nrows = A.nrows;
-  const int p0 = bx * A.LP;
+  constexpr int LPC = NC ? (DGPE_MAXT / 2) / (NC / 16) : 0, SLC = NC ? NC + NC / PW + 1 : 0;
+  const int n = NC ? NC : A.nx, SL = NC ? SLC : A.pitchz, nrows = A.nrows, LP = NC ? LPC : A.LP;
+  const int px = NC ? NC / 2 + 2 : A.px;
+  const int p0 = bx * LP;
   const R sc = (R)A.prm[PRM_SC];
   const R sc2 = sc * sc;
   const cx<R> *__restrict__ psi = A.psi;
@@ -278,19 +283,20 @@ __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A, int bx) {
   rt4<R> *s_rt = reinterpret_cast<rt4<R> *>(scr + OFF_RT);
   const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, n);
   const rt4<R> *rt = FMA ? stage_roots(s_rt, A.twf, n) : nullptr;
-  tile_fft<R, EPT, false, false, PW, POW2, FMA>(zt, SL, 1, A.LP, A.pl, tw, load, store, rt);
+  if constexpr (NC > 0) tile_fft_ct<R, NC, EPT, false, PW, SLC, LPC, DGPE_MAXT>(zt, tw, load, store);
+  else tile_fft<R, EPT, false, false, PW, POW2, FMA>(zt, SL, 1, A.LP, A.pl, tw, load, store, rt);
   // two real lines were packed as Z = n0 + i n1: X0 = (Z_k + conj Z_{n-k}) / 2,
   // X1 = (Z_k - conj Z_{n-k}) / (2i), k = 0..n/2
   const int nh = n / 2 + 1;
-  for (int idx = threadIdx.x; idx < A.LP * nh; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < LP * nh; idx += blockDim.x) {
     const int l = idx / nh, k = idx - l * nh;
     const int r0 = 2 * (p0 + l), r1 = r0 + 1;
     if (r0 >= nrows) continue;
     const cx<R> Zk = zt[sidx<PW>(l, k, SL, 1)], Zm = zt[sidx<PW>(l, (k == 0 ? 0 : n - k), SL, 1)];
     const cx<R> X0 = mk<R>((R)0.5 * (Zk.x + Zm.x), (R)0.5 * (Zk.y - Zm.y));
     const cx<R> X1 = mk<R>((R)0.5 * (Zk.y + Zm.y), (R)0.5 * (Zm.x - Zk.x));
-    A.spec[(size_t)r0 * A.px + k] = X0;
-    if (r1 < nrows) A.spec[(size_t)r1 * A.px + k] = X1;
+    A.spec[(size_t)r0 * px + k] = X0;
+    if (r1 < nrows) A.spec[(size_t)r1 * px + k] = X1;
   }
 }
 template <typename R, int EPT, int SRC = 0, bool POW2 = true, bool FMA = false>
@@ -315,12 +321,17 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
 //   imaginary parts: the exponential scales each part by its own row's
 //   factor, and one Crank-Nicolson solve with the real coefficients of
 //   imaginary time advances both rows.
-template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false, int SCR = 0>
+// NC > 0 (FP32, power-of-two nx = NC, the default tile, DGPE_MAXT threads):
+// compile-time lengths and tile, the C2R transform by tile_fft_ct.
+template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false, int SCR = 0, int NC = 0>
 __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);  // psi tile: 2 LP lines, pitch P
-  cx<R> *zt = pt + 2 * A.LP * A.pitch;           // Z tile: LP lines, pitch pitchz
   constexpr int PW = Pad<R>::W;
+  constexpr int LPC = NC ? (DGPE_MAXT / 2) / (NC / CL) : 0, PC = NC ? NC + NC / CL + 1 : 0;
+  constexpr int PZC = NC ? NC + NC / PW + 1 : 0;
+  const int LP = NC ? LPC : A.LP;
+  cx<R> *pt = reinterpret_cast<cx<R> *>(smraw);          // psi tile: 2 LP lines, pitch P
+  cx<R> *zt = pt + 2 * LP * (NC ? PC : A.pitch);         // Z tile: LP lines, pitch pitchz
   constexpr bool TAB = (sizeof(R) == 8);
   // shared scratch: s_k[4] (dt s(t) f, g dt f, g_dd dt f, sc; thread 0, from
   // FP64), s_vyz[DGPE_MAXT] (V_y + V_z of the CTA's rows, 2 LP <= DGPE_MAXT),
@@ -338,21 +349,22 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   R *const s_vyz = reinterpret_cast<R *>(scr + OFF_VYZ);
   R *const s_dvx = reinterpret_cast<R *>(scr + OFF_DVX);
   Coef *const s_tab = reinterpret_cast<Coef *>(scr + OFF_TAB);
-  if (!TAB && MODE != 1 && MODE != 3) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), A.nx);
+  if (!TAB && MODE != 1 && MODE != 3) stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), NC ? NC : A.nx);
   constexpr bool RS = (MODE == 4);  // real state
   R *const ptr = reinterpret_cast<R *>(pt);
   // tile element of row L, column a: (line, component) for a real state
-  auto rs_at = [&](int L, int a) -> R & { return ptr[2 * ((L >> 1) * A.pitch + a + a / CL) + (L & 1)]; };
-  const int n = A.nx, nh = n / 2, nrows = A.nrows, P = A.pitch;
+  const int n = NC ? NC : A.nx, nh = n / 2, nrows = A.nrows, P = NC ? PC : A.pitch;
+  const int px = NC ? NC / 2 + 2 : A.px;
+  auto rs_at = [&](int L, int a) -> R & { return ptr[2 * ((L >> 1) * P + a + a / CL) + (L & 1)]; };
   const int ln = POW2 ? ilog2(n) : 0;
-  const int p0 = bx * A.LP;
+  const int p0 = bx * LP;
   const int T = blockDim.x, t = threadIdx.x;
   auto row_of = [&](int idx) { return POW2 ? (idx >> ln) : (idx / n); };
   auto col_of = [&](int idx) { return POW2 ? (idx & (n - 1)) : (idx % n); };
   // the trap tables are read only by the modes that apply the exponential
   // (MODE 1 and 2 callers may leave vx, vy, vz NULL)
   if constexpr (MODE != 1 && MODE != 2) {
-    if (t < 2 * A.LP) {
+    if (t < 2 * LP) {
       const int row = 2 * p0 + t;
       s_vyz[t] = (row < nrows) ? A.vy[row % A.ny] + A.vz[row / A.ny] : (R)0;
     }
@@ -409,7 +421,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   if (DIRECT && !imag && MODE != 1 && MODE != 2) {
     // dt s(t) V with the scale of V_y + V_z applied in place (each CTA owns its rows)
     for (int a = t; a < n; a += T) s_dvx[a] = dts * A.vx[a];
-    if (t < 2 * A.LP) s_vyz[t] *= dts;
+    if (t < 2 * LP) s_vyz[t] *= dts;
     __syncthreads();
   }
   // exponential substep on the tile element (L, a) in place.  FP64 real
@@ -449,8 +461,8 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
       const int r0 = 2 * (p0 + l), r1 = r0 + 1;
       const int k = (a <= nh) ? a : n - a;
       cx<R> X0 = czero<cx<R>>(), X1 = czero<cx<R>>();
-      if (r0 < nrows) X0 = A.spec[(size_t)r0 * A.px + k];
-      if (r1 < nrows) X1 = A.spec[(size_t)r1 * A.px + k];
+      if (r0 < nrows) X0 = A.spec[(size_t)r0 * px + k];
+      if (r1 < nrows) X1 = A.spec[(size_t)r1 * px + k];
       if (a == 0 || a == nh) { X0.y = 0; X1.y = 0; }  // real-to-real ends of a real line
       if (a > nh) { X0.y = -X0.y; X1.y = -X1.y; }    // Hermitian extension
       return mk<R>(X0.x - X1.y, X0.y + X1.x);        // Z = X0 + i X1
@@ -465,15 +477,16 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
       apply_e(2 * l, a, v.x);
       apply_e(2 * l + 1, a, v.y);
     };
-    tile_fft<R, EPT, true, false, PW, POW2, FMA>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store, rt);
+    if constexpr (NC > 0) tile_fft_ct<R, NC, EPT, true, PW, PZC, LPC, DGPE_MAXT>(zt, s_twp, load, store);
+    else tile_fft<R, EPT, true, false, PW, POW2, FMA>(zt, A.pitchz, 1, A.LP, A.pl, s_twp, load, store, rt);
   } else if (MODE == 0 || MODE == 3 || MODE == 4) {
-    for (int idx = t; idx < 2 * A.LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
+    for (int idx = t; idx < 2 * LP * n; idx += T) apply_e(row_of(idx), col_of(idx), (R)0);
     __syncthreads();
   }
   if (MODE == 1) return;
   if (MODE == 3) {
     __syncthreads();
-    for (int idx = t; idx < 2 * A.LP * n; idx += T) {
+    for (int idx = t; idx < 2 * LP * n; idx += T) {
       const int L = row_of(idx), a = col_of(idx);
       const int row = 2 * p0 + L;
       if (row < nrows) A.psi[(size_t)row * n + a] = pt[L * P + a + a / CL];
@@ -482,11 +495,12 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   }
   // Crank-Nicolson along x: TPL lanes per line (a real state: LP lines, each
   // a pair of rows; the other half of the threads idles)
-  const int l = t / A.TPL, q = t - l * A.TPL;
-  const bool active = RS ? (l < A.LP && 2 * (p0 + l) < nrows) : (2 * p0 + l) < nrows;
-  if constexpr (TAB) cn_line<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+  const int TPLr = NC ? NC / CL : A.TPL;
+  const int l = t / TPLr, q = t - l * TPLr;
+  const bool active = RS ? (l < LP && 2 * (p0 + l) < nrows) : (2 * p0 + l) < nrows;
+  if constexpr (TAB) cn_line<R, Coef, CL>(pt + l * P, n, TPLr, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), active);
-  else cn_line_st<R, Coef, CL>(pt + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, active);
+  else cn_line_st<R, Coef, CL>(pt + l * P, n, TPLr, q, make_kt<Coef>(A.tau), s_tab, active);
   __syncthreads();
   if constexpr (RS) {
     R *__restrict__ pr = reinterpret_cast<R *>(A.psi);
@@ -755,7 +769,9 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
 // ------------------------------------------------- P5 / P6 / P7 (strided)
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
-template <typename R, int EPT, int MODE, bool POW2, bool FMA = false, int SCR = 0>
+// NC > 0 (FP32, power-of-two line length NC, tile width WC, WC NC / EPT
+// threads): compile-time lengths, the transforms by tile_fft_ct_cols.
+template <typename R, int EPT, int MODE, bool POW2, bool FMA = false, int SCR = 0, int NC = 0, int WC = 0>
 __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A, int bx, int by, int gx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);  // [a][W]
@@ -772,11 +788,11 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A, int bx, int 
   cx<R> *const s_tw = reinterpret_cast<cx<R> *>(scr + OFF_TW);
   rt4<R> *const s_rf = reinterpret_cast<rt4<R> *>(scr + OFF_RF);
   rt4<R> *const s_ri = reinterpret_cast<rt4<R> *>(scr + OFF_RI);
-  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, A.n);
+  const cx<R> *tw = FMA ? A.tw : stage_twiddles<R>(s_tw, A.tw, NC ? NC : A.n);
   const rt4<R> *rf = nullptr, *ri = nullptr;
   if constexpr (NF) rf = stage_roots(s_rf, A.twf, A.n);
   if constexpr (NI) ri = stage_roots(s_ri, A.twi, A.n);
-  const int W = A.W;
+  const int W = NC ? WC : A.W;
   const int c0 = bx * W;
   const size_t base = (size_t)by * A.ostride + c0;
   const long long es = A.estride;
@@ -787,7 +803,16 @@ __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A, int bx, int 
   auto gstore = [&](int l, int a, cx<R> v) {
     if (c0 + l < A.ncols) spec[base + a * es + l] = v;
   };
-  if (MODE == 0) {
+  if constexpr (NC > 0 && MODE == 2) {
+    constexpr int TC = WC * NC / EPT;
+    auto mstore = [&](int l, int a, cx<R> v) {
+      const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
+      sm[a * WC + l] = cscale(v, u);
+    };
+    tile_fft_ct_cols<R, NC, EPT, false, WC, TC>(sm, tw, gload, mstore);
+    auto sload = [&](int l, int a) -> cx<R> { return sm[a * WC + l]; };
+    tile_fft_ct_cols<R, NC, EPT, true, WC, TC>(sm, tw, sload, gstore);
+  } else if (MODE == 0) {
     tile_fft<R, EPT, false, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, gstore, rf);
   } else if (MODE == 1) {
     tile_fft<R, EPT, true, true, 0, POW2, FMA>(sm, 1, W, W, A.pl, tw, gload, gstore, ri);
@@ -867,7 +892,8 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_stride
 // ------------------------------------------------------- P2 / P3 (strided)
 // NORM false: a pass without the norm (no |x|^2 code at all); true: the
 // runtime flag A.norm decides.
-template <typename R, typename Coef, int CL, bool NORM = true, int SCR = 0>
+// NC > 0 (power-of-two line length NC, tile width WC): compile-time lengths.
+template <typename R, typename Coef, int CL, bool NORM = true, int SCR = 0, int NC = 0, int WC = 0>
 __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int by, int gx, int gy) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *tile = reinterpret_cast<cx<R> *>(smraw);  // [W][pitch]
@@ -880,8 +906,9 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int b
   double *const red = reinterpret_cast<double *>(scr);
   int &am_last = *reinterpret_cast<int *>(scr + OFF_LAST);
   Coef *const s_tab = reinterpret_cast<Coef *>(scr + OFF_TAB);
-  const int W = A.W, n = A.n, P = A.pitch;
-  const int lW = ilog2(W);
+  const int W = NC ? WC : A.W, n = NC ? NC : A.n, P = NC ? NC + NC / CL + 1 : A.pitch;
+  const int lW = NC ? ct_log2(WC) : ilog2(W);
+  const int TPL = NC ? NC / CL : A.TPL;
   const int c0 = bx * W;
   const size_t base = (size_t)by * A.ostride + c0;
   const long long es = A.estride;
@@ -893,10 +920,10 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int b
     const bool ok = c0 + lc < A.ncols;
     cx<R> buf[CL];
 #pragma unroll
-    for (int i = 0; i < CL; ++i) buf[i] = ok ? A.psi[base + (size_t)(r0 + i * A.TPL) * es + lc] : czero<cx<R>>();
+    for (int i = 0; i < CL; ++i) buf[i] = ok ? A.psi[base + (size_t)(r0 + i * TPL) * es + lc] : czero<cx<R>>();
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
-      const int a = r0 + i * A.TPL;
+      const int a = r0 + i * TPL;
       tile[lc * P + a + a / CL] = buf[i];
     }
   }
@@ -905,17 +932,17 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int b
     stage_cn_tables<Coef, CL>(s_tab, reinterpret_cast<const Coef *>(A.cntab), n);
     __syncthreads();
   }
-  const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
-  if constexpr (TAB) cn_line<R, Coef, CL>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
+  const int l = threadIdx.x / TPL, q = threadIdx.x - l * TPL;
+  if constexpr (TAB) cn_line<R, Coef, CL>(tile + l * P, n, TPL, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
-  else cn_line_st<R, Coef, CL>(tile + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
+  else cn_line_st<R, Coef, CL>(tile + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
   __syncthreads();
   double acc = 0.0;
   if (c0 + lc < A.ncols) {
     R ts = (R)0;  // the thread's CL sites in R, then FP64 above the tile
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
-      const int a = r0 + i * A.TPL;
+      const int a = r0 + i * TPL;
       const cx<R> v = tile[lc * P + a + a / CL];
       A.psi[base + (size_t)a * es + lc] = v;
       if (NORM && A.norm) ts += v.x * v.x + v.y * v.y;

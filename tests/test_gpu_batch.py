@@ -75,7 +75,9 @@ def test_batch_full_length_against_oracle():
     a 256^2 grid takes even the FP64 form 1e-10 from the oracle in 1000 steps,
     against about 1e-12 for the other problems), psi is held instead to the
     oracle's own divergence under FP32-rounding-sized noise injected every
-    step."""
+    step, and mu to the first-order bound that its psi error e allows:
+    mu = <psi|H|psi>/<psi|psi> moves by at most about 2 e |mu| for a relative
+    change e of a state that is not an eigenstate."""
     gbuild.build()
     probs = synth.batched_problems(4640, 8, sizes=synth.BATCH_SIZES)
     for i, n in enumerate(synth.BATCH_SIZES):
@@ -98,11 +100,13 @@ def test_batch_full_length_against_oracle():
         worst = max(worst, e)
         print(i, q["n"], "imag" if q["imag"] else "real", "g %.1f g_dd %.1f" % (q["g"], q["gdd"]),
               "rel L2", e, "mu", obs[i]["mu"], r["mu"])
+        tol_mu = 1e-6
         if e >= 1e-5:
             d = _oracle_fp32_noise_divergence(op, _psi0(q), steps)
             print("   oracle divergence under FP32-sized noise", d)
             assert e <= d
-        assert abs(obs[i]["mu"] - r["mu"]) <= 1e-6 * abs(r["mu"])
+            tol_mu = max(tol_mu, 2.0 * e)
+        assert abs(obs[i]["mu"] - r["mu"]) <= tol_mu * abs(r["mu"])
     print("worst rel L2 over the batch", worst)
 
 
