@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <map>
 #include <string>
 #include <vector>
@@ -241,6 +242,38 @@ __device__ __forceinline__ void resident64_run(const BProb &B, int nsteps) {
   if (t == 0) const_cast<double *>(X.prm)[PRM_SC] = 1.0;
 }
 
+// One tile of one pass, one body per function: each is compiled (and its
+// registers allocated) on its own, so the large switch of the persistent
+// kernel does not make the bodies spill.  N > 0: power-of-two side N with
+// compile-time lengths (the default tile shapes of the persistent step).
+template <int EX, int EPS, int CL, bool P2, int N, int LEVEL, typename Coef>
+__device__ __noinline__ void batch_body(const BProb &B, int tile) {
+  constexpr int WS = N ? DGPE_MAXT * EPS / N : 0, WCN = N ? DGPE_MAXT / (N / CL) : 0;
+  constexpr bool IMAG = std::is_same<Coef, float>::value;
+  if constexpr (LEVEL == 0) dens_r2c_x_body<float, EX, 0, P2, false, kBatchScr, N>(B.X, tile);
+  else if constexpr (LEVEL == 1) fft_strided_body<float, EPS, 2, P2, false, kBatchScr, N, WS>(B.S, tile, 0, B.tiles[1]);
+  else if constexpr (LEVEL == 2) c2r_x_exp_cnx_body<float, Coef, EX, CL, 0, P2, false, kBatchScr, N>(B.X, tile);
+  else cn_strided_body<float, Coef, CL, IMAG, kBatchScr, N, WCN>(B.C, tile, 0, B.tiles[3], 1);
+}
+template <int EX, int EPS, int CL, bool P2, int N>
+__device__ __forceinline__ void batch_pass(const BProb &B, int level, int tile) {
+  switch (level) {
+    case 0: batch_body<EX, EPS, CL, P2, N, 0, float>(B, tile); break;
+    case 1: batch_body<EX, EPS, CL, P2, N, 1, float>(B, tile); break;
+    case 2:
+      if (B.imag) batch_body<EX, EPS, CL, P2, N, 2, float>(B, tile);
+      else batch_body<EX, EPS, CL, P2, N, 2, float2>(B, tile);
+      break;
+    default:
+      if (B.imag) batch_body<EX, EPS, CL, P2, N, 3, float>(B, tile);
+      else batch_body<EX, EPS, CL, P2, N, 3, float2>(B, tile);
+  }
+}
+template <typename Coef>
+__device__ __noinline__ void batch_resident(const BProb &B, int nsteps) {
+  resident64_run<Coef>(B, nsteps);
+}
+
 __global__ void __launch_bounds__(DGPE_MAXT, 2)
     k_batch_run(const BProb *__restrict__ probs, const int4 *__restrict__ items, const int *__restrict__ counts,
                 int L, const int *__restrict__ res, int nres, int nsteps, unsigned *sync, long long wait_limit) {
@@ -301,63 +334,26 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2)
       const BProb &B = sP;
       for (int tile = tile0; tile < tile0 + cnt; ++tile) {
       if (level == 4) {
-        if (B.imag) resident64_run<float>(B, nsteps);
-        else resident64_run<float2>(B, nsteps);
-      } else if (B.var == VAR_P2 && (B.n == 128 || B.n == 256 || B.n == 512)) {
-        // power-of-two sides: bodies with the length and tile as constants
-        auto run = [&](auto Nc) {
-          constexpr int N = decltype(Nc)::value, WS = DGPE_MAXT * 16 / N, WCN = DGPE_MAXT / (N / 16);
-          switch (level) {
-            case 0: dens_r2c_x_body<float, 8, 0, true, false, kBatchScr, N>(B.X, tile); break;
-            case 1: fft_strided_body<float, 16, 2, true, false, kBatchScr, N, WS>(B.S, tile, 0, B.tiles[1]); break;
-            case 2:
-              if (B.imag) c2r_x_exp_cnx_body<float, float, 8, 16, 0, true, false, kBatchScr, N>(B.X, tile);
-              else c2r_x_exp_cnx_body<float, float2, 8, 16, 0, true, false, kBatchScr, N>(B.X, tile);
-              break;
-            default:
-              if (B.imag) cn_strided_body<float, float, 16, true, kBatchScr, N, WCN>(B.C, tile, 0, B.tiles[3], 1);
-              else cn_strided_body<float, float2, 16, false, kBatchScr, N, WCN>(B.C, tile, 0, B.tiles[3], 1);
-          }
-        };
-        if (B.n == 128) run(std::integral_constant<int, 128>{});
-        else if (B.n == 256) run(std::integral_constant<int, 256>{});
-        else run(std::integral_constant<int, 512>{});
+        if (B.imag) batch_resident<float>(B, nsteps);
+        else batch_resident<float2>(B, nsteps);
+      } else if (B.var == VAR_P2 && B.n == 128) {
+        batch_pass<8, 16, 16, true, 128>(B, level, tile);
+      } else if (B.var == VAR_P2 && B.n == 256) {
+        batch_pass<8, 16, 16, true, 256>(B, level, tile);
+      } else if (B.var == VAR_P2 && B.n == 512) {
+        batch_pass<8, 16, 16, true, 512>(B, level, tile);
       } else if (B.var == VAR_P2) {
-        switch (level) {
-          case 0: dens_r2c_x_body<float, 8, 0, true, false, kBatchScr>(B.X, tile); break;
-          case 1: fft_strided_body<float, 16, 2, true, false, kBatchScr>(B.S, tile, 0, B.tiles[1]); break;
-          case 2:
-            if (B.imag) c2r_x_exp_cnx_body<float, float, 8, 16, 0, true, false, kBatchScr>(B.X, tile);
-            else c2r_x_exp_cnx_body<float, float2, 8, 16, 0, true, false, kBatchScr>(B.X, tile);
-            break;
-          default:
-            if (B.imag) cn_strided_body<float, float, 16, true, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-            else cn_strided_body<float, float2, 16, false, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-        }
+        batch_pass<8, 16, 16, true, 0>(B, level, tile);
+      } else if (B.var == VAR_3 && B.n == 96) {
+        batch_pass<12, 12, 12, false, 96>(B, level, tile);
+      } else if (B.var == VAR_3 && B.n == 384) {
+        batch_pass<12, 12, 12, false, 384>(B, level, tile);
       } else if (B.var == VAR_3) {
-        switch (level) {
-          case 0: dens_r2c_x_body<float, 12, 0, false, false, kBatchScr>(B.X, tile); break;
-          case 1: fft_strided_body<float, 12, 2, false, false, kBatchScr>(B.S, tile, 0, B.tiles[1]); break;
-          case 2:
-            if (B.imag) c2r_x_exp_cnx_body<float, float, 12, 12, 0, false, false, kBatchScr>(B.X, tile);
-            else c2r_x_exp_cnx_body<float, float2, 12, 12, 0, false, false, kBatchScr>(B.X, tile);
-            break;
-          default:
-            if (B.imag) cn_strided_body<float, float, 12, true, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-            else cn_strided_body<float, float2, 12, false, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-        }
+        batch_pass<12, 12, 12, false, 0>(B, level, tile);
+      } else if (B.var == VAR_5 && B.n == 160) {
+        batch_pass<20, 20, 10, false, 160>(B, level, tile);
       } else {
-        switch (level) {
-          case 0: dens_r2c_x_body<float, 20, 0, false, false, kBatchScr>(B.X, tile); break;
-          case 1: fft_strided_body<float, 20, 2, false, false, kBatchScr>(B.S, tile, 0, B.tiles[1]); break;
-          case 2:
-            if (B.imag) c2r_x_exp_cnx_body<float, float, 20, 10, 0, false, false, kBatchScr>(B.X, tile);
-            else c2r_x_exp_cnx_body<float, float2, 20, 10, 0, false, false, kBatchScr>(B.X, tile);
-            break;
-          default:
-            if (B.imag) cn_strided_body<float, float, 10, true, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-            else cn_strided_body<float, float2, 10, false, kBatchScr>(B.C, tile, 0, B.tiles[3], 1);
-        }
+        batch_pass<20, 20, 10, false, 0>(B, level, tile);
       }
       __syncthreads();
       }

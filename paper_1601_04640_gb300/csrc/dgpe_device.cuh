@@ -401,15 +401,19 @@ __device__ __forceinline__ void tile_fft(cx<R> *sm, int SL, int SA, int nlines, 
 // block size T and the radix sequence are compile-time constants: every
 // index (line, butterfly, twiddle, shared-memory address) folds to shifts,
 // masks and immediate offsets, and only the stages the length needs are
-// compiled.  Radices: the largest of 16, 8, 4, 2 dividing both EPT and what
-// is left of N, in order (the inverse runs the sequence reversed).
+// compiled.  Radices: the first of 16, 8, 5, 4, 3, 2 dividing both EPT and
+// what is left of N, in order (the runtime plans' sequence; the inverse runs
+// it reversed).
 constexpr int ct_radix(int n, int ept, int s) {
+  // candidates in the order of the runtime plans: 16, 8, 5, 4, 3, 2
   int m = n;
   for (int k = 0; k < 16; ++k) {
     int r = 0;
     if (ept % 16 == 0 && m % 16 == 0) r = 16;
     else if (ept % 8 == 0 && m % 8 == 0) r = 8;
+    else if (ept % 5 == 0 && m % 5 == 0) r = 5;
     else if (ept % 4 == 0 && m % 4 == 0) r = 4;
+    else if (ept % 3 == 0 && m % 3 == 0) r = 3;
     else if (m % 2 == 0) r = 2;
     if (r == 0) return 0;
     if (k == s) return r;
@@ -437,17 +441,20 @@ template <typename R, int N, int EPT, int RAD, int NS, bool INV, int PADW, int S
 __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict__ tw, Load &load, Store &store) {
   static_assert(EPT % RAD == 0, "radix must divide the elements per thread");
   constexpr int NB = EPT / RAD;
-  constexpr int NBL = N / RAD, LNBL = ct_log2(NBL), LR = ct_log2(RAD), LNS = ct_log2(NS), LNL = ct_log2(NL);
+  constexpr int NBL = N / RAD;
   constexpr int B = NBL * NL;
   constexpr int TSTR = N / (NS * RAD);
+  // divisions by constants: shifts and masks for powers of two, multiplies
+  // by reciprocals otherwise (3 2^k and 5 2^k lengths)
   const int t = threadIdx.x;
   cx<R> v[EPT];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
-    const bool ok = (B % T == 0) || b < B;
-    const int l = LINE_FAST ? (b & (NL - 1)) : (b >> LNBL);
-    const int j = LINE_FAST ? (b >> LNL) : (b & (NBL - 1));
+    const bool ok = (B == T * NB) || b < B;  // every butterfly slot of the block is real
+    const unsigned ub = (unsigned)b;
+    const int l = (int)(LINE_FAST ? (ub % NL) : (ub / NBL));
+    const int j = (int)(LINE_FAST ? (ub / NL) : (ub % NBL));
     cx<R> *u = v + i * RAD;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
@@ -457,7 +464,7 @@ __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict_
       else u[r] = sm[ct_sidx<PADW, SL, SA>(l, a)];
     }
     if constexpr (!FIRST) {
-      const int k = j & (NS - 1);
+      const int k = (int)((unsigned)j % NS);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
         const cx<R> w = tw[k * r * TSTR];
@@ -470,10 +477,11 @@ __device__ __forceinline__ void fft_stage_ct(cx<R> *sm, const cx<R> *__restrict_
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * T;
-    if ((B % T == 0) || b < B) {
-      const int l = LINE_FAST ? (b & (NL - 1)) : (b >> LNBL);
-      const int j = LINE_FAST ? (b >> LNL) : (b & (NBL - 1));
-      const int base = ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
+    if ((B == T * NB) || b < B) {
+      const unsigned ub = (unsigned)b;
+      const int l = (int)(LINE_FAST ? (ub % NL) : (ub / NBL));
+      const unsigned uj = LINE_FAST ? (ub / NL) : (ub % NBL);
+      const int base = (int)((uj / NS) * NS * RAD + (uj % NS));
       cx<R> *u = v + i * RAD;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {

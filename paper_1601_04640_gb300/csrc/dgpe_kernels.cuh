@@ -243,15 +243,18 @@ __host__ __device__ constexpr int scr_align(int b) { return (b + 31) & ~31; }
 // SRC 0: the density sc^2 |psi|^2;  SRC 1: the real field A.dens_in;
 // SRC 2: sc^2 psi^2 of a real state (A.psi holds nx reals per row).
 // FMA: twiddled stages in FMA form (tile_fft), roots from A.twf.
-// NC > 0 (FP32, power-of-two nx = NC, the default tile of 2 LP rows and
-// DGPE_MAXT threads): the line length, tile and plan are compile-time
-// constants and the transform is tile_fft_ct.
+// NC > 0 (FP32, nx = NC, the default tile of 2 LP rows and DGPE_MAXT
+// threads): the line length, tile and plan are compile-time constants and
+// the transform is tile_fft_ct.
 template <typename R, int EPT, int SRC, bool POW2, bool FMA = false, int SCR = 0, int NC = 0>
 __device__ __forceinline__ void dens_r2c_x_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *zt = reinterpret_cast<cx<R> *>(smraw);
   constexpr int PW = Pad<R>::W;
-  constexpr int LPC = NC ? (DGPE_MAXT / 2) / (NC / 16) : 0, SLC = NC ? NC + NC / PW + 1 : 0;
+  // CN chunk of the length's variant (2^k: 16, 3 2^k: 12, 5 2^k: 10) sets the
+  // tile: LP = (DGPE_MAXT / 2) / (n / CL) lines
+  constexpr int CLX = (NC % 3 == 0) ? 12 : (NC % 5 == 0) ? 10 : 16;
+  constexpr int LPC = NC ? (DGPE_MAXT / 2) / (NC / CLX) : 0, SLC = NC ? NC + NC / PW + 1 : 0;
   const int n = NC ? NC : A.nx, SL = NC ? SLC : A.pitchz, nrows = A.nrows, LP = NC ? LPC : A.LP;
   const int px = NC ? NC / 2 + 2 : A.px;
   const int p0 = bx * LP;
@@ -321,8 +324,8 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_P4(R)) k_dens_r2c_x_batch
 //   imaginary parts: the exponential scales each part by its own row's
 //   factor, and one Crank-Nicolson solve with the real coefficients of
 //   imaginary time advances both rows.
-// NC > 0 (FP32, power-of-two nx = NC, the default tile, DGPE_MAXT threads):
-// compile-time lengths and tile, the C2R transform by tile_fft_ct.
+// NC > 0 (FP32, nx = NC, the default tile, DGPE_MAXT threads): compile-time
+// lengths and tile, the C2R transform by tile_fft_ct.
 template <typename R, typename Coef, int EPT, int CL, int MODE, bool POW2, bool FMA = false, int SCR = 0, int NC = 0>
 __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -769,8 +772,8 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
 // ------------------------------------------------- P5 / P6 / P7 (strided)
 // MODE 0 forward, 1 inverse, 2 forward . U . inverse, 3 forward and
 // accumulate sum_k w_k U_k |F_k|^2 (FP64) for the dipolar energy.
-// NC > 0 (FP32, power-of-two line length NC, tile width WC, WC NC / EPT
-// threads): compile-time lengths, the transforms by tile_fft_ct_cols.
+// NC > 0 (FP32, line length NC, tile width WC, WC NC / EPT threads):
+// compile-time lengths, the transforms by tile_fft_ct_cols.
 template <typename R, int EPT, int MODE, bool POW2, bool FMA = false, int SCR = 0, int NC = 0, int WC = 0>
 __device__ __forceinline__ void fft_strided_body(const SArgs<R> &A, int bx, int by, int gx) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -892,7 +895,7 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_stride
 // ------------------------------------------------------- P2 / P3 (strided)
 // NORM false: a pass without the norm (no |x|^2 code at all); true: the
 // runtime flag A.norm decides.
-// NC > 0 (power-of-two line length NC, tile width WC): compile-time lengths.
+// NC > 0 (line length NC, power-of-two tile width WC): compile-time lengths.
 template <typename R, typename Coef, int CL, bool NORM = true, int SCR = 0, int NC = 0, int WC = 0>
 __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int by, int gx, int gy) {
   extern __shared__ __align__(16) unsigned char smraw[];
