@@ -218,6 +218,9 @@ def main():
                     help="precision forms to time (the first listed is the top-level line)")
     ap.add_argument("--prep-steps", type=int, default=None,
                     help="imaginary-time preparation steps (default: the workload's)")
+    ap.add_argument("--problems", type=int, default=512,
+                    help="batched2d: the first K problems of the seeded sweep (default: all 512; a smaller K "
+                         "is a profiling case, not the workload)")
     args = ap.parse_args()
     args.steps_default = "--steps" not in " ".join(sys.argv[1:])
     wl = dict(WORKLOADS[args.workload])
@@ -604,7 +607,7 @@ def bench_batched(args, wl, world, rank, local):
     torch.cuda.set_device(local)
     gbuild.build()
     stream = torch.cuda.Stream()
-    sweep = synth.batched_problems(4640, 512)
+    sweep = synth.batched_problems(4640, 512)[:max(1, min(512, args.problems))]
     parts = shard.partition(sweep, world)
     mine = parts[rank]
     probs = [sweep[i] for i in mine]
