@@ -122,3 +122,53 @@ def test_autograd_function():
         _, dg, dc = dgpe.dgpe_fidelity_gradient(s.h, psi0, target, 16, 4, len(cm))
     assert abs(g.grad.item() - 2.0 * dg) <= 1e-12 * abs(dg)
     assert np.allclose(c.grad.numpy(), 2.0 * np.array(dc), rtol=1e-12, atol=0)
+
+
+def test_adjoint_config_full_length_fd():
+    """The adjoint workload at its own size and length: 128^3, h = 0.15, cigar
+    trap, g = 200, g_dd = 60, dt = 1e-3, V(t) = V0 (1 + sum_m c_m sin(m t)) with
+    the seeded c_1..c_8, 1000 steps, checkpoints every 32 steps.  FP64 form:
+    the reverse sweep's dF/dg and dF/dc_m against central finite differences
+    of the GPU forward at the benchmark spec's bound (1e-6 relative); the FP32-bulk
+    gradient against the FP64 one."""
+    gbuild.build()
+    n, h, nu = (128, 128, 128), (0.15,) * 3, (1.0, 1.0, 0.5)
+    g0, gdd, dt, K, every = 200.0, 60.0, 1e-3, 1000, 32
+    cm = list(synth.trap_modulation(160104640, 8, 0.05))
+    psi0 = synth.gaussian_state(n, h, (1.0, 1.0, 0.5), 0.01, 1)
+    target = synth.gaussian_state(n, h, (1.1, 0.9, 0.5), 0.01, 2)
+    w = np.prod(h)
+
+    def fid(s):
+        s.set_psi(psi0)
+        s.step(K)
+        return abs(w * np.vdot(target, s.get_psi())) ** 2
+
+    with dgpe.Solver(3, n, h, nu, g0, gdd, dt, False, True) as s:
+        s.set_trap_modulation(cm)
+        F, dg, dc = dgpe.dgpe_fidelity_gradient(s.h, psi0, target, K, every, len(cm))
+        s.set_trap_modulation(cm)
+        assert abs(fid(s) - F) <= 1e-12 * F
+        eps = 1e-3
+        s.set_g(g0 + eps); fp = fid(s)
+        s.set_g(g0 - eps); fm = fid(s)
+        s.set_g(g0)
+        fd = (fp - fm) / (2 * eps)
+        print("F", F, "dF/dg adjoint", dg, "fd", fd, "rel", abs(dg - fd) / abs(fd))
+        assert abs(dg - fd) <= 1e-6 * abs(fd)
+        eps = 1e-4
+        for m in (0, 1, 4, 7):
+            cp = list(cm); cp[m] += eps
+            cq = list(cm); cq[m] -= eps
+            s.set_trap_modulation(cp); fp = fid(s)
+            s.set_trap_modulation(cq); fm = fid(s)
+            fd = (fp - fm) / (2 * eps)
+            print("dF/dc_%d adjoint" % (m + 1), dc[m], "fd", fd, "rel", abs(dc[m] - fd) / abs(fd))
+            assert abs(dc[m] - fd) <= 1e-6 * abs(fd) + 1e-12 * F
+    with dgpe.Solver(3, n, h, nu, g0, gdd, dt, False, False) as s:
+        s.set_trap_modulation(cm)
+        F32, g32, c32 = dgpe.dgpe_fidelity_gradient(s.h, psi0, target, K, every, len(cm))
+    print("FP32 bulk: F", F32, "dF/dg", g32)
+    assert abs(F32 - F) <= 1e-5 * F
+    assert abs(g32 - dg) <= 1e-3 * abs(dg)
+    assert np.max(np.abs(np.array(c32) - dc)) <= 1e-3 * np.max(np.abs(dc))
