@@ -759,6 +759,32 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
+// ------------------------------------------ tensor-map copies (TMA tiles)
+// A 3D box of a tensor described by a CUtensorMap (passed as a
+// __grid_constant__ kernel parameter; `tmap` is its generic address) moved
+// between global and shared memory by the TMA unit.  Loads complete on an
+// mbarrier with the box's byte count (out-of-range elements are filled with
+// zeros); stores clip to the tensor's bounds, are committed as a bulk group,
+// and the issuing thread waits for the group to have read its shared memory
+// before that memory is reused.  Coordinates are in elements, innermost
+// first; the innermost one times the element size is a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void *tmap, int c0, int c1, int c2, const void *src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(tmap),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // --------------------------------------------------- FP64 block reductions
 // Deterministic for a fixed block size: warp tree, then warp totals in order.
 __device__ __forceinline__ double warp_sum(double v) {

@@ -165,6 +165,24 @@ inline double wavenumber(int j, int n, double h) {
 #ifndef DGPE_FFT_FMA_F32
 #define DGPE_FFT_FMA_F32 0  // FP32 density and strided transforms in FMA form too (measured 3 % slower)
 #endif
+// cuTensorMapEncodeTiled from the driver, found once through the runtime's
+// entry-point query (no link-time dependency on the driver library).
+typedef CUresult (*TensorMapEncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                           const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                           CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                           CUtensorMapFloatOOBfill);
+inline TensorMapEncodeTiledFn tensor_map_encoder() {
+  static TensorMapEncodeTiledFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<TensorMapEncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
 // Call f(N) with N = n as a compile-time constant for the power-of-two line
 // lengths of the length-specialised kernels (0 when n is not one of them).
 template <class F> int with_pow2_len(int n, F &&f) {
@@ -225,6 +243,10 @@ template <typename R> struct EngineT : Engine {
   bool p4_pipe = false;
   int p4_grid = 0;
   size_t p4_smem = 0;
+  // ... and the TMA-tiled strided transforms (k_fft_tma): tensor maps of the
+  // half spectrum for lines along y and along z
+  bool tma_fft = false;
+  CUtensorMap tm_y{}, tm_z{};
   struct CnCfg {
     int n, ncols, W, TPL, C, pitch, T;
     long long es, os;
@@ -744,7 +766,7 @@ template <typename R> struct EngineT : Engine {
       });
       if (rc) return rc;
     }
-    return DGPE_OK;
+    return setup_tma();
   }
 
   // ------------------------------------------------------------- launches
@@ -793,9 +815,117 @@ template <typename R> struct EngineT : Engine {
       }) != 0;
     }
   }
+  // FP32, power-of-two lengths: tensor maps of the half spectrum (kx, y, z;
+  // kx valid columns, rows of px elements) for the TMA-tiled transforms.
+  // Not fatal when unavailable: the length-specialised kernels run instead.
+  int tma_grid[2] = {0, 0};
+  template <int AX, int N, int WW> int tma_attrs(int &grid) {
+    const size_t sm = 2 * sizeof(Cx) * (size_t)WW * N + 128;
+    int r;
+    if constexpr (AX == 1) {  // lines along y: FFT_y, IFFT_y (3D) and FFT_y.U.IFFT_y (2D)
+      if ((r = smem_attr(k_fft_tma<EPT_S, 0, N, WW, AX>, sm))) return r;
+      if ((r = smem_attr(k_fft_tma<EPT_S, 1, N, WW, AX>, sm))) return r;
+    }
+    if ((r = smem_attr(k_fft_tma<EPT_S, 2, N, WW, AX>, sm))) return r;
+    int occ = 0;
+    DGPE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_tma<EPT_S, 2, N, WW, AX>, WW * N / EPT_S, sm));
+    grid = nsm * occ;
+    return DGPE_OK;
+  }
+  template <int AX> int tma_axis(const FtCfg &f, int &grid) {
+    return with_pow2_len(f.n, [&](auto Nc) -> int {
+      constexpr int N = decltype(Nc)::value;
+      if constexpr (N == 0) {
+        return DGPE_EUNSUPPORTED;
+      } else {
+        if (f.W == 16) {
+          if constexpr (16 * N / EPT_S <= DGPE_MAXT_FFT) return this->template tma_attrs<AX, N, 16>(grid);
+        } else if (f.W == 8) {
+          if constexpr (8 * N / EPT_S <= DGPE_MAXT_FFT) return this->template tma_attrs<AX, N, 8>(grid);
+        }
+        return DGPE_EUNSUPPORTED;
+      }
+    });
+  }
+  int setup_tma() {
+    if constexpr (sizeof(R) != 4) {
+      return DGPE_OK;
+    } else {
+      tma_fft = false;
+      if (!has_dip || (p.flags & DGPE_FLAG_P1_ONESHOT)) return DGPE_OK;
+      if (var[1] != VAR_P2 || (dim == 3 && var[2] != VAR_P2)) return DGPE_OK;
+      TensorMapEncodeTiledFn enc = tensor_map_encoder();
+      if (!enc) return DGPE_OK;
+      const cuuint64_t dims[3] = {(cuuint64_t)ncol_spec, (cuuint64_t)ny, (cuuint64_t)nz};
+      const cuuint64_t strides[2] = {(cuuint64_t)px * sizeof(Cx), (cuuint64_t)ny * px * sizeof(Cx)};
+      const cuuint32_t es[3] = {1, 1, 1};
+      auto rows = [](int n) { return (cuuint32_t)(n / ((n + 255) / 256)); };
+      const cuuint32_t by[3] = {(cuuint32_t)fy.W, rows(ny), 1};
+      if (enc(&tm_y, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, spec, dims, strides, by, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return DGPE_OK;
+      if (dim == 3) {
+        const cuuint32_t bz[3] = {(cuuint32_t)fz.W, 1, rows(nz)};
+        if (enc(&tm_z, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, spec, dims, strides, bz, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          return DGPE_OK;
+      }
+      int r = this->template tma_axis<1>(fy, tma_grid[0]);
+      if (r == DGPE_EUNSUPPORTED) return DGPE_OK;
+      if (r) return r;
+      if (dim == 3) {
+        r = this->template tma_axis<2>(fz, tma_grid[1]);
+        if (r == DGPE_EUNSUPPORTED) return DGPE_OK;
+        if (r) return r;
+      }
+      tma_fft = tma_grid[0] > 0 && (dim == 2 || tma_grid[1] > 0);
+      return DGPE_OK;
+    }
+  }
+  bool launch_fft_tma(const FtCfg &f, int mode, const SArgs<R> &A, cudaStream_t s) {
+    if constexpr (sizeof(R) != 4) {
+      return false;
+    } else {
+      if (!tma_fft || mode > 2) return false;
+      const int ncb = (int)f.grid.x, ntiles = (int)(f.grid.x * f.grid.y);
+      return with_pow2_len(f.n, [&](auto Nc) -> int {
+        constexpr int N = decltype(Nc)::value;
+        if constexpr (N == 0) {
+          return 0;
+        } else {
+          auto go = [&](auto Wc) -> int {
+            constexpr int WW = decltype(Wc)::value;
+            if constexpr (WW * N / EPT_S <= DGPE_MAXT_FFT) {
+              const size_t sm = 2 * sizeof(Cx) * (size_t)WW * N + 128;
+              const int T = WW * N / EPT_S;
+              double *tf = prm + PRM_TIMEOUT;
+              if (f.axis == 1) {
+                const int g = std::max(1, std::min(ntiles, tma_grid[0]));
+                if (mode == 0) k_fft_tma<EPT_S, 0, N, WW, 1><<<g, T, sm, s>>>(tm_y, A, ncb, ntiles, tf);
+                else if (mode == 1) k_fft_tma<EPT_S, 1, N, WW, 1><<<g, T, sm, s>>>(tm_y, A, ncb, ntiles, tf);
+                else k_fft_tma<EPT_S, 2, N, WW, 1><<<g, T, sm, s>>>(tm_y, A, ncb, ntiles, tf);
+              } else {
+                const int g = std::max(1, std::min(ntiles, tma_grid[1]));
+                if (mode != 2) return 0;
+                k_fft_tma<EPT_S, 2, N, WW, 2><<<g, T, sm, s>>>(tm_z, A, ncb, ntiles, tf);
+              }
+              return 1;
+            } else {
+              return 0;
+            }
+          };
+          if (f.W == 16) return go(std::integral_constant<int, 16>{});
+          if (f.W == 8) return go(std::integral_constant<int, 8>{});
+          return 0;
+        }
+      }) != 0;
+    }
+  }
   int launch_fft(const FtCfg &f, int mode, cudaStream_t s) {
     SArgs<R> A = sargs(f);
-    if (launch_fft_ct(f, mode, A, s)) {
+    if (launch_fft_tma(f, mode, A, s) || launch_fft_ct(f, mode, A, s)) {
       launched(1);
       DGPE_LCK(__func__);
       return DGPE_OK;

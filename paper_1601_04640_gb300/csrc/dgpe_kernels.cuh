@@ -12,6 +12,8 @@
 // A 2D step = P4, P6 along y, P1, P2 (CN_y is the final pass).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type of a TMA descriptor parameter)
+
 #include "dgpe_device.cuh"
 
 // Kernels have internal linkage (unnamed namespace): every translation unit
@@ -592,7 +594,11 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p4_pipe(const __grid_constant_
     const bool ok = mbar_wait_bounded(&bar[k], (ph >> k) & 1u, DGPE_WAIT_LIMIT);
     ph ^= 1u << k;
     if (__syncthreads_or(!ok)) {
-      if (t == 0) *timeout_flag = 1.0;
+      if (t == 0) {
+        // the copy into the other stage, if one was issued, lands (bounded wait) before the block exits
+        if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[k ^ 1], (ph >> (k ^ 1)) & 1u, DGPE_WAIT_LIMIT);
+        *timeout_flag = 1.0;
+      }
       return;
     }
     const Cx *__restrict__ sp = stg0 + k * ROWS * N;
@@ -890,6 +896,105 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_stride
     auto sload = [&](int l, int a) -> Cx { return sm[a * W + l]; };
     tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, gstore);
   }
+}
+
+// FP32 strided transforms with TMA tiles (power-of-two lengths): persistent
+// CTAs walk the tiles; one thread loads a tile of W spectrum columns x N
+// rows into shared memory with tensor-map copies (the dense box layout
+// [row][column] is the transform's column-tile layout), two tiles ahead in
+// two buffers, and writes the transformed tile back with tensor-map stores,
+// so no thread issues a global load or store of the spectrum.  AXIS 1: the
+// lines run along y (coordinates kx, y = row, z = outer index); AXIS 2: along
+// z (kx, y = outer index, z = row).  Boxes are at most 256 rows (N = 512 takes
+// two).  Columns beyond the spectrum's width load as zeros and are not
+// stored.  Waits are bounded as in the x-line pipelines.
+template <int EPT, int MODE, int N, int W, int AXIS>
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, 2)
+    k_fft_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ SArgs<float> A, int ncb, int ntiles,
+              double *timeout_flag) {
+  typedef float R;
+  typedef float2 Cx;
+  constexpr int T = W * N / EPT, TILE = W * N;
+  constexpr int NBOX = (N + 255) / 256, BOXR = N / NBOX;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // tiles 128-byte aligned inside the dynamic allocation (it has 128 spare bytes)
+  Cx *const buf0 = reinterpret_cast<Cx *>(smraw + ((128 - (smem_u32(smraw) & 127)) & 127));
+  __shared__ unsigned long long bar[2];
+  __shared__ __align__(16) Cx s_tw[N];
+  const int t = threadIdx.x;
+  auto issue = [&](int tile, int k) {  // thread 0
+    const int c0 = (tile % ncb) * W, o = tile / ncb;
+    Cx *dst = buf0 + k * TILE;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[k], (unsigned)(sizeof(Cx) * TILE));
+#pragma unroll
+    for (int b = 0; b < NBOX; ++b) {
+      if (AXIS == 1) tma_load_3d(dst + b * BOXR * W, &tm, c0, b * BOXR, o, &bar[k]);
+      else tma_load_3d(dst + b * BOXR * W, &tm, c0, o, b * BOXR, &bar[k]);
+    }
+  };
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  if (t == 0) {
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+  for (int i = t; i < N; i += T) s_tw[i] = A.tw[i];
+  __syncthreads();
+  unsigned ph = 0u;  // bit k: the phase parity buffer k waits for next
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
+    const bool ok = mbar_wait_bounded(&bar[k], (ph >> k) & 1u, DGPE_WAIT_LIMIT);
+    ph ^= 1u << k;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        bulk_wait_all();
+        if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[k ^ 1], (ph >> (k ^ 1)) & 1u, DGPE_WAIT_LIMIT);
+        *timeout_flag = 1.0;
+      }
+      return;
+    }
+    Cx *const sm = buf0 + k * TILE;
+    const int c0 = (tile % ncb) * W, o = tile / ncb;
+    auto sload = [&](int l, int a) -> Cx { return sm[a * W + l]; };
+    auto sstore = [&](int l, int a, Cx v) { sm[a * W + l] = v; };
+    if constexpr (MODE == 0) {
+      tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, sload, sstore);
+    } else if constexpr (MODE == 1) {
+      tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, sstore);
+    } else {
+      const size_t base = (size_t)o * A.ostride + c0;
+      const long long es = A.estride;
+      auto mstore = [&](int l, int a, Cx v) {
+        const R u = (c0 + l < A.ncols) ? A.U[base + a * es + l] : (R)0;
+        sm[a * W + l] = cscale(v, u);
+      };
+      tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, sload, mstore);
+      tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, sstore);
+    }
+    // the transformed tile goes back by tensor-map stores
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+      for (int b = 0; b < NBOX; ++b) {
+        if (AXIS == 1) tma_store_3d(&tm, c0, b * BOXR, o, sm + b * BOXR * W);
+        else tma_store_3d(&tm, c0, o, b * BOXR, sm + b * BOXR * W);
+      }
+      bulk_commit();
+      const int next2 = tile + 2 * gridDim.x;
+      if (next2 < ntiles) {
+        bulk_wait_read_all();  // the store has read this buffer before it is refilled
+        issue(next2, k);
+      }
+    }
+  }
+  if (t == 0) bulk_wait_all();
+  __syncthreads();
+  if (t == 0) { mbar_inval(&bar[0]); mbar_inval(&bar[1]); }
 }
 
 // ------------------------------------------------------- P2 / P3 (strided)
