@@ -185,7 +185,7 @@ __device__ __forceinline__ void resident64_run(const BProb &B, int nsteps) {
     // Crank-Nicolson along x: TPL lanes per row
     {
       const int l = t / TPL, q = t - l * TPL;
-      cn_line_st<R, Coef, CL>(ps + l * P, N, TPL, q, ktx, tabx, true);
+      cn_line_st<R, Coef, CL>(ps + l * P, N, TPL, q, ktx, tabx, true, X.cnd);
       __syncthreads();
     }
     // Crank-Nicolson along y, one thread per column, increment form:
@@ -484,6 +484,7 @@ int configure(dgpe_batch *b, Cls &c, int LP, int sW, int cW) {
     q.psi = e->psi; q.cntab = e->cntab[1]; q.prm = e->prm; q.partial = e->partial; q.counter = e->counter;
     q.step = e->dstep; q.estride = cc.es; q.ostride = cc.os; q.n = cc.n; q.ncols = cc.ncols; q.W = cW;
     q.TPL = cc.TPL; q.C = cc.C; q.pitch = cc.pitch; q.final_pass = 1; q.norm = c.imag; q.tau = e->tau[1];
+    q.cnd = e->cn_dlim[1];
     Cn.push_back(q);
   }
   BCK(cudaMemcpy(c.dX, X.data(), sizeof(XArgs<float>) * X.size(), cudaMemcpyHostToDevice));
@@ -641,6 +642,7 @@ int build_persistent(dgpe_batch *b) {
       q.C.counter = e->counter; q.C.step = e->dstep; q.C.estride = e->cn[1].es; q.C.ostride = e->cn[1].os;
       q.C.n = e->cn[1].n; q.C.ncols = e->cn[1].ncols; q.C.W = cW; q.C.TPL = e->cn[1].TPL; q.C.C = e->cn[1].C;
       q.C.pitch = e->cn[1].pitch; q.C.final_pass = 1; q.C.norm = c.imag; q.C.tau = e->tau[1];
+      q.C.cnd = e->cn_dlim[1];
       q.var = c.var;
       q.imag = c.imag;
       q.n = c.n;

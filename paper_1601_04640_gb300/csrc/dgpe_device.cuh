@@ -624,11 +624,20 @@ __device__ __forceinline__ double2 coef_fma(double a, double2 v, double2 w) {
 __device__ __forceinline__ double2 coef_fma(double2 a, double2 v, double2 w) {
   return make_double2(fma(a.x, v.x, fma(-a.y, v.y, w.x)), fma(a.x, v.y, fma(a.y, v.x, w.y)));
 }
+//
+// dlim > 0 limits the Kogge-Stone scans to the rounds d < dlim: the inflow of
+// a chunk then gathers the dlim chunks before it exactly and drops the rest,
+// whose weights are products of at least dlim whole-chunk products P_chunk.
+// The host picks dlim from rho = max |P_chunk| so that the dropped part,
+// at most rho^dlim / (1 - rho) of the largest chunk value, is below 2^-32
+// of it (kt = dt / (4 h^2) small: rho is tiny and a chunk needs only its
+// neighbour's value); dlim <= 0 runs all rounds.
 template <typename R, typename Coef, int CL>
 __device__ __forceinline__ void cn_line_st(cx<R> *line, int n, int TPL, int q, Coef kt,
-                                           const Coef *__restrict__ tab, bool active) {
+                                           const Coef *__restrict__ tab, bool active, int dlim = 0) {
   typedef cx<R> Cx;
   const int TS = n + n / CL + 1;
+  const int DL = (dlim > 0 && dlim < TPL) ? dlim : TPL;
   const int a0 = q * CL;
   Cx *lp = line + a0 + q;                 // padded address of element a0
   const Coef *tm = tab + a0 + q, *ta = tm + TS, *tp = ta + TS, *tq = tp + TS;
@@ -653,7 +662,7 @@ __device__ __forceinline__ void cn_line_st(cx<R> *line, int n, int TPL, int q, C
   }
   Coef P = active ? tp[CL - 1] : coef_zero<Coef>();
   Cx Y = acc;
-  for (int d = 1; d < TPL; d <<= 1) {
+  for (int d = 1; d < DL; d <<= 1) {
     Coef Pn = shfl_up(P, d, TPL);
     Cx Yn = shfl_up(Y, d, TPL);
     if (q >= d) { Y = coef_fma(P, Yn, Y); P = coef_prod(P, Pn); }
@@ -670,7 +679,7 @@ __device__ __forceinline__ void cn_line_st(cx<R> *line, int n, int TPL, int q, C
   }
   Coef Q = active ? tq[0] : coef_zero<Coef>();
   Cx W = acc;
-  for (int d = 1; d < TPL; d <<= 1) {
+  for (int d = 1; d < DL; d <<= 1) {
     Coef Qn = shfl_down(Q, d, TPL);
     Cx Wn = shfl_down(W, d, TPL);
     if (q + d < TPL) { W = coef_fma(Q, Wn, W); Q = coef_prod(Q, Qn); }

@@ -230,6 +230,8 @@ template <typename R> struct EngineT : Engine {
   unsigned *counter = nullptr;
   FftPlan plx{}, ply{}, plz{}, plx_s{};
   double tau[3] = {0, 0, 0};
+  // chunk-scan reach of the FP32 chunk-parallel CN solve per axis (cn_line_st)
+  int cn_dlim[3] = {0, 0, 0};
 
   // pass configurations
   int x_LP = 0, x_T = 0, x_TPL = 0, x_C = 0, x_pitchz = 0, x_pitch = 0, x_grid = 0;
@@ -578,12 +580,25 @@ template <typename R> struct EngineT : Engine {
       //   mu = 1 / (1 + 2kt - kt (alpha_{k-1} + alpha_{n-2-k}))
       const int kmid = n / 2;
       const zd mu = 1.0 / (b - kt * (al[kmid - 1] + al[n - 2 - kmid]));
+      double rho = 0.0;  // largest whole-chunk product |alpha_a0 ... alpha_a0+C-1|
       for (int c0 = 0; c0 < n; c0 += C) {
         zd pr = 1.0;
         for (int i = c0; i < c0 + C; ++i) { pr *= al[i]; P[i] = pr; }
         pr = 1.0;
         for (int i = c0 + C - 1; i >= c0; --i) { pr *= al[i]; Q[i] = pr; }
+        rho = std::max(rho, std::abs(P[c0 + C - 1]));
       }
+      // scan rounds d < dl reach dl chunks back; what they drop is at most
+      // rho^dl / (1 - rho) of the largest chunk value: keep it below 2^-32
+      int dl = 1;
+      if (rho >= 0.5) {
+        dl = 0;  // all rounds
+      } else {
+        double e = rho;
+        while (dl < 64 && e / (1.0 - rho) > 0x1p-32) { e *= e; dl <<= 1; }
+        if (dl >= 64) dl = 0;
+      }
+      cn_dlim[a] = dl;
       if (!cntab[a]) {
         int rc = dalloc((Cx **)&cntab[a], 4 * (size_t)n + 1);
         if (rc) return rc;
@@ -777,6 +792,7 @@ template <typename R> struct EngineT : Engine {
     A.pl = plx; A.nx = nx; A.ny = ny; A.nrows = nrows; A.px = px; A.LP = x_LP;
     A.pitchz = x_pitchz; A.pitch = x_pitch; A.TPL = x_TPL; A.C = x_C;
     A.imag = imag; A.has_dip = has_dip ? 1 : 0; A.tau = tau[0]; A.dtf = 1.0;
+    A.cnd = cn_dlim[0];
     return A;
   }
   SArgs<R> sargs(const FtCfg &f) const {
@@ -784,6 +800,13 @@ template <typename R> struct EngineT : Engine {
     A.spec = spec; A.U = U; A.partial = dip_part; A.tw = tw[f.axis]; A.pl = f.pl;
     A.twf = twf[f.axis]; A.twi = twi[f.axis];
     A.estride = f.es; A.ostride = f.os; A.n = f.n; A.ncols = ncol_spec; A.W = f.W; A.nxh = nx / 2;
+    if (dim == 3) {
+      A.uq[0] = (float)(2.0 * M_PI / (nx * p.h[0]));
+      A.uq[1] = (float)(2.0 * M_PI / (ny * p.h[1]));
+      A.uq[2] = (float)(2.0 * M_PI / (nz * p.h[2]));
+      A.uq[3] = (float)((4.0 * M_PI / 3.0) / (double)nsites);
+    }
+    A.uny = ny;
     return A;
   }
   // FP32, power-of-two length, modes 0-2: the length-specialised transform
@@ -984,6 +1007,7 @@ template <typename R> struct EngineT : Engine {
     A.step = dstep; A.estride = c.es; A.ostride = c.os; A.n = c.n; A.ncols = c.ncols; A.W = c.W;
     A.TPL = c.TPL; A.C = c.C; A.pitch = c.pitch; A.final_pass = final_pass ? 1 : 0;
     A.norm = (final_pass && imag) ? 1 : 0; A.tau = adjoint ? -tau[axis] : tau[axis];
+    A.cnd = cn_dlim[axis];
     const int ncb = (int)c.grid.x, ntiles = (int)(c.grid.x * c.grid.y);
     if (launch_cn_ct(c, axis, A, ncb, ntiles, s)) {
       launched(1);
@@ -1056,6 +1080,7 @@ template <typename R> struct EngineT : Engine {
     if (mode == 2) {
       A.cntab = cntab_adj[0];
       A.tau = -tau[0];
+      A.cnd = cn_dlim[0];
     }
     with_xvar(var[0], [&](auto CLc, auto EXc, auto P2c) -> int {
       constexpr int CL = decltype(CLc)::value, EX = decltype(EXc)::value;

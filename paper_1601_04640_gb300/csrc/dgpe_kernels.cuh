@@ -52,6 +52,7 @@ template <typename R> struct XArgs {  // x-line passes
   int nx, ny, nrows, px, LP;
   int pitchz, pitch, TPL, C;
   int imag, has_dip;
+  int cnd;  // chunk-scan reach of the CN_x solve (0: all lanes)
   double tau;
   double dtf;  // fraction of dt taken by the exponential substep (1: a full step)
 };
@@ -65,6 +66,10 @@ template <typename R> struct SArgs {  // strided FFT passes over the spectrum
   FftPlan pl;
   long long estride, ostride;
   int n, ncols, W, nxh;
+  // 3D dipolar kernel from the wavenumbers (FP32 tensor-map z-pass):
+  // dq_x, dq_y, dq_z (2 pi / (n h) per axis), (4 pi / 3) / N_sites; ny
+  float uq[4];
+  int uny;
 };
 
 template <typename R> struct CArgs {  // strided CN passes
@@ -77,6 +82,7 @@ template <typename R> struct CArgs {  // strided CN passes
   long long estride, ostride;
   int n, ncols, W, TPL, C, pitch;
   int final_pass, norm;
+  int cnd;  // chunk-scan reach of the CN solve (0: all lanes)
   double tau;
 };
 
@@ -505,7 +511,7 @@ __device__ __forceinline__ void c2r_x_exp_cnx_body(const XArgs<R> &A, int bx) {
   const bool active = RS ? (l < LP && 2 * (p0 + l) < nrows) : (2 * p0 + l) < nrows;
   if constexpr (TAB) cn_line<R, Coef, CL>(pt + l * P, n, TPLr, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), active);
-  else cn_line_st<R, Coef, CL>(pt + l * P, n, TPLr, q, make_kt<Coef>(A.tau), s_tab, active);
+  else cn_line_st<R, Coef, CL>(pt + l * P, n, TPLr, q, make_kt<Coef>(A.tau), s_tab, active, A.cnd);
   __syncthreads();
   if constexpr (RS) {
     R *__restrict__ pr = reinterpret_cast<R *>(A.psi);
@@ -713,6 +719,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
   __syncthreads();
   const R dts = s_k[0], gdt = s_k[1], gdddt = s_k[2], sc = s_k[3];
   const int imag = A.imag;
+  constexpr bool RT = sizeof(Coef) == sizeof(Cx);
   unsigned phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
     const int r0 = tile * ROWS;
@@ -729,7 +736,9 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
     }
     // exponential substep: staged psi (dense) -> padded tile
     auto apply_e = [&](int L, int a, R phi) {
-      const cx<R> v = cscale(sp[(L << LN) + a], sc);
+      // real time (complex CN coefficients): the lazy norm scale is 1 (only
+      // imaginary-time norm passes change it; a mode switch folds it into psi)
+      const cx<R> v = RT ? sp[(L << LN) + a] : cscale(sp[(L << LN) + a], sc);
       const R dens = v.x * v.x + v.y * v.y;
       const R th = dts * (svx[a] + s_vyz[L]) + gdt * dens + gdddt * phi;
       pt[L * P + a + a / CL] = nonlinear_factor<R>(v, th, imag);
@@ -762,7 +771,8 @@ __global__ void __launch_bounds__(DGPE_MAXT, 2) k_p1_pipe(const __grid_constant_
     if (t == 0 && next < ntiles) issue(next);
     // Crank-Nicolson along x: TPL lanes per line
     const int l = t / TPL, q = t - l * TPL;
-    cn_line_st<R, Coef, CL>(pt + l * P, N, TPL, q, make_kt<Coef>(A.tau), tab, full || (r0 + l) < nrows);
+    cn_line_st<R, Coef, CL>(pt + l * P, N, TPL, q, make_kt<Coef>(A.tau), tab, full || (r0 + l) < nrows,
+                            A.cnd);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < CL; ++i) {
@@ -908,8 +918,15 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_MINB_FFT_F32) k_fft_stride
 // z (kx, y = outer index, z = row).  Boxes are at most 256 rows (N = 512 takes
 // two).  Columns beyond the spectrum's width load as zeros and are not
 // stored.  Waits are bounded as in the x-line pipelines.
+#ifndef DGPE_TMA_MINB
+#define DGPE_TMA_MINB 3  // resident blocks per SM the tensor-map transforms are compiled for
+#endif
+// The 3D z-pass (MODE 2, AXIS 2) evaluates U(k) = (4 pi / 3)(3 k_z^2 / k^2 - 1)
+// / N_sites in FP32 from the wavenumbers (U(0) = 0) instead of reading the
+// table: four bytes less per spectrum element and no global load inside the
+// transform pair.
 template <int EPT, int MODE, int N, int W, int AXIS>
-__global__ void __launch_bounds__(DGPE_MAXT_FFT, 2)
+__global__ void __launch_bounds__(DGPE_MAXT_FFT, DGPE_TMA_MINB)
     k_fft_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ SArgs<float> A, int ncb, int ntiles,
               double *timeout_flag) {
   typedef float R;
@@ -964,6 +981,19 @@ __global__ void __launch_bounds__(DGPE_MAXT_FFT, 2)
     if constexpr (MODE == 0) {
       tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, sload, sstore);
     } else if constexpr (MODE == 1) {
+      tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, sstore);
+    } else if constexpr (AXIS == 2) {
+      // tile: kx = c0 + l, ky = o, kz = row a
+      const int jy = (o <= A.uny / 2) ? o : o - A.uny;
+      const R qy = (R)jy * A.uq[1];
+      const R qy2 = qy * qy, dqx = A.uq[0], dqz = A.uq[2], pref = A.uq[3];
+      auto mstore = [&](int l, int a, Cx v) {
+        const R qx = (R)(c0 + l) * dqx, qz = (R)((a <= N / 2) ? a : a - N) * dqz;
+        const R qz2 = qz * qz, k2 = fmaf(qx, qx, qy2) + qz2;
+        const R u = (k2 > (R)0) ? pref * ((R)3 * qz2 / k2 - (R)1) : (R)0;
+        sm[a * W + l] = cscale(v, u);
+      };
+      tile_fft_ct_cols<R, N, EPT, false, W, T>(sm, s_tw, sload, mstore);
       tile_fft_ct_cols<R, N, EPT, true, W, T>(sm, s_tw, sload, sstore);
     } else {
       const size_t base = (size_t)o * A.ostride + c0;
@@ -1043,7 +1073,7 @@ __device__ __forceinline__ void cn_strided_body(const CArgs<R> &A, int bx, int b
   const int l = threadIdx.x / TPL, q = threadIdx.x - l * TPL;
   if constexpr (TAB) cn_line<R, Coef, CL>(tile + l * P, n, TPL, q, make_kt<Coef>(A.tau),
                                       reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
-  else cn_line_st<R, Coef, CL>(tile + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
+  else cn_line_st<R, Coef, CL>(tile + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols, A.cnd);
   __syncthreads();
   double acc = 0.0;
   if (c0 + lc < A.ncols) {
@@ -1146,7 +1176,8 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_strided_pipe(
     const int l = threadIdx.x / A.TPL, q = threadIdx.x - l * A.TPL;
     if constexpr (TAB) cn_line<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau),
                                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
-    else cn_line_st<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
+    else cn_line_st<R, Coef, CL>(tb + l * P, n, A.TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols,
+                                 A.cnd);
     __syncthreads();
     if (c0 + lc < A.ncols) {
       cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;
@@ -1239,7 +1270,7 @@ __global__ void __launch_bounds__(DGPE_MAXT, DGPE_MINB_CN(R)) k_cn_pipe_ct(const
     const int l = threadIdx.x / TPL, q = threadIdx.x - l * TPL;
     if constexpr (TAB) cn_line<R, Coef, CL>(tb + l * P, n, TPL, q, make_kt<Coef>(A.tau),
                                         reinterpret_cast<const Coef *>(A.cntab), c0 + l < A.ncols);
-    else cn_line_st<R, Coef, CL>(tb + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols);
+    else cn_line_st<R, Coef, CL>(tb + l * P, n, TPL, q, make_kt<Coef>(A.tau), s_tab, c0 + l < A.ncols, A.cnd);
     __syncthreads();
     if (c0 + lc < A.ncols) {
       cx<R> *dst = A.psi + (size_t)o * A.ostride + c0 + lc;

@@ -170,6 +170,29 @@ def test_cn_only(form, imag):
     assert e < TOL_PSI[fp64]
 
 
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("dt", [0.01, 0.2, 2.0, 20.0])
+def test_cn_only_scan_reach(imag, dt):
+    """FP32 chunk-parallel CN substeps alone (g = g_dd = 0, no trap) over
+    kt = dt / (4 h^2) = 0.0625 ... 125.  The scan across the chunks of a line
+    runs only as many rounds as the whole-chunk products |alpha|^16 need: one
+    neighbour at small kt (|alpha| ~ kt), every round at large kt (|alpha|
+    near 1).  Each regime must agree with the oracle's Thomas solve, within
+    a few FP32 ulps times the solve's condition number 1 + 4 kt (the
+    imaginary-time substeps damp high modes by up to that factor and the norm
+    restores them)."""
+    n, h = (256, 64, 32), (0.2, 0.2, 0.2)
+    kt = dt / (4 * 0.04)
+    op, kc, psi0 = make_case(3, n, h, (0, 0, 0), 0, 0, dt, imag, kernel="none", noise=0.3,
+                             widths=(2.0, 1.5, 1.0))
+    psi, _ = gpu_run(3, n, h, (0, 0, 0), 0, 0, dt, imag, False, kc, psi0, 3)
+    ref = oracle.step(op, psi0, 0, 3)
+    e = rel_l2(psi, ref)
+    tol = max(TOL_PSI[False], 4 * (1 + 4 * kt) * 2.0 ** -24)
+    print("kt", kt, "rel L2", e, "tol", tol)
+    assert e < tol
+
+
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_observables_parity(fp64, dim):
