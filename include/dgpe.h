@@ -117,7 +117,12 @@ extern "C" {
                                    (density + R2C; C2R, exponential, CN_x) as
                                    one CTA per tile instead of the default
                                    persistent CTAs fed by bulk asynchronous
-                                   copies (same arithmetic) */
+                                   copies, and the strided transforms as
+                                   register-fed tiles instead of persistent
+                                   CTAs fed by tensor-map copies (same
+                                   arithmetic, except that the 3D z-pass
+                                   then reads U(k) from its FP32 table
+                                   instead of evaluating it in FP32) */
 
 #define DGPE_FLAG_BATCH_CLASSES 64u /* batched form (set on any problem): step
                                    the batch as per-size-class batched kernels

@@ -1191,7 +1191,9 @@ template <typename R> struct EngineT : Engine {
     switch (v[i]) {
       case PS_DENS_R2C: return N * SP + sp * S;
       case PS_FFT_Y: case PS_IFFT_Y: return 2.0 * sp * S;
-      case PS_FFT_Z_U: case PS_FFT_Y_U: return 2.0 * sp * S + ub;
+      // the FP32 3D tensor-map z-pass evaluates U(k) instead of reading it
+      case PS_FFT_Z_U: return 2.0 * sp * S + ((tma_fft && dim == 3) ? 0.0 : ub);
+      case PS_FFT_Y_U: return 2.0 * sp * S + ub;
       case PS_P1: case PS_P1_NOCN: return (has_dip ? sp * S : 0.0) + 2.0 * N * SP;
       default: return 2.0 * N * SP;
     }
