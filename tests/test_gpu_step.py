@@ -694,3 +694,44 @@ def test_p1_pipelined_matches_oneshot_and_oracle(imag, case):
         print(kernel, "pipelined", e0, "one-shot", e1, "between", d)
         assert e0 < TOL_PSI[False] and e1 < TOL_PSI[False]
         assert d < 1e-6
+
+
+TMA_CASES = [
+    (3, (64, 512, 32), (0.2, 0.05, 0.3), (1.0, 1.0, 1.5)),
+    (3, (32, 64, 512), (0.3, 0.2, 0.04), (1.0, 1.2, 0.7)),
+    (3, (96, 64, 64), (0.2, 0.25, 0.25), (1.0, 1.1, 1.3)),
+    (2, (64, 512), (0.2, 0.05), (1.0, 1.4)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TMA_CASES)))
+def test_tensor_map_transforms_match_register_fed_and_oracle(case):
+    """FP32 bulk, power-of-two y and z lines: the strided transforms fed by
+    tensor-map tiles (the default; the 3D z-pass evaluates U(k)) against the
+    register-fed kernels with the U table (DGPE_FLAG_P1_ONESHOT) and against
+    the oracle, for Phi_d and for 4 real-time steps.  The cases take 512-point
+    lines (two boxes per tile, 8-column tiles) along y and along z, a spectrum
+    width that leaves a ragged last tile (nx = 96: 49 columns in tiles of 16),
+    and the 2D y-pass FFT_y.U.IFFT_y."""
+    dim, n, h, nu = TMA_CASES[case]
+    op, kc, psi0 = make_case(dim, n, h, nu, 60.0, 30.0, 1e-3, False)
+    phis, outs = [], []
+    for flags in (0, dgpe.DGPE_FLAG_P1_ONESHOT):
+        with dgpe.Solver(dim, n, h, nu, 60.0, 30.0, 1e-3, False, False, kernel=kc, flags=flags) as s:
+            s.set_psi(psi0)
+            phis.append(s.dipolar_potential())
+            s.step(4)
+            outs.append(s.get_psi())
+    # the oracle sees the state the FP32 form holds (psi rounded once)
+    dens = np.abs(psi0.astype(np.complex64).astype(np.complex128)) ** 2
+    phi_ref = oracle.dipolar_potential(op, dens)
+    scale = np.max(np.abs(phi_ref))
+    ep = [np.max(np.abs(ph - phi_ref)) / scale for ph in phis]
+    dp = np.max(np.abs(phis[0] - phis[1])) / scale
+    ref = oracle.step(op, psi0, 0, 4)
+    e0, e1 = rel_l2(outs[0], ref), rel_l2(outs[1], ref)
+    d = rel_l2(outs[0], outs[1])
+    print("Phi_d vs oracle", ep, "between", dp, "| psi vs oracle", e0, e1, "between", d)
+    assert max(ep) < 1e-5 and dp < 2e-6
+    assert e0 < TOL_PSI[False] and e1 < TOL_PSI[False]
+    assert d < 1e-6
